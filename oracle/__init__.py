@@ -1,0 +1,243 @@
+"""FP64 CPU oracle for the pulse-noise many-spin step (arXiv:1610.04914).
+
+TEST INFRASTRUCTURE ONLY: the test-suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package; the GPU library never
+does, and this package never imports the GPU library.
+
+The arithmetic lives in ``spin_oracle.c`` (plain C, double precision, one site
+at a time, compiled with ``-ffp-contract=off``).  This module only builds it
+with gcc, loads it with ctypes and marshals numpy arrays.
+
+Spin states are numpy arrays of shape (3, nz, ny, nx) (component, z, y, x),
+i.e. structure-of-arrays with x fastest.
+
+Parity status (what pins each function) is stated in the C source and in the
+``-m "not gpu"`` tests under ``tests/test_oracle_*.py``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "spin_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+RK4, RK5_BUTCHER, RK2_MIDPOINT, HEUN = 0, 1, 2, 3
+
+
+def build(force: bool = False) -> str:
+    """Compile spin_oracle.c into liboracle.so next to it (gcc, no fast-math)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+        ("integrator", ctypes.c_int32), ("precession", ctypes.c_int32),
+        ("R", ctypes.c_int32), ("renorm", ctypes.c_int32), ("replica", ctypes.c_int32),
+        ("J", ctypes.c_double), ("D", ctypes.c_double), ("H", ctypes.c_double * 3),
+        ("lambda_", ctypes.c_double), ("T", ctypes.c_double), ("dt", ctypes.c_double),
+        ("seed", ctypes.c_uint64),
+    ]
+
+
+@dataclass
+class Params:
+    """Problem statement of one lattice run (gamma = mu0 = k_B = 1)."""
+    nx: int
+    ny: int
+    nz: int
+    J: float = 1.0
+    D: float = 0.0
+    H: tuple = (0.0, 0.0, 0.0)
+    lam: float = 0.1
+    T: float = 1.0
+    dt: float = 0.1
+    R: int = 10                    # steps per noise interval, Delta t = R dt
+    integrator: int = RK4
+    precession: int = 1            # 0: slow (overdamped) equation
+    renorm: int = 1
+    seed: int = 1
+    replica: int = 0
+
+    @property
+    def N(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    def c(self) -> _Params:
+        return _Params(self.nx, self.ny, self.nz, self.integrator, self.precession,
+                       self.R, self.renorm, self.replica, self.J, self.D,
+                       (ctypes.c_double * 3)(*self.H), self.lam, self.T, self.dt,
+                       self.seed & 0xFFFFFFFFFFFFFFFF)
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = ctypes.CDLL(build())
+        P = ctypes.POINTER
+        d, u64, i64 = ctypes.c_double, ctypes.c_uint64, ctypes.c_int64
+        L.orc_philox4x64.argtypes = [P(u64), P(u64), P(u64)]
+        L.orc_gauss3.argtypes = [P(u64), P(d)]
+        L.orc_noise_gauss.argtypes = [u64, i64, i64, i64, P(d)]
+        L.orc_heff.argtypes = [P(_Params), P(d), P(d), P(d)]
+        L.orc_rhs.argtypes = [P(_Params), P(d), P(d), P(d)]
+        L.orc_integrate.argtypes = [P(_Params), P(d), P(d)]
+        L.orc_renormalise.argtypes = [P(_Params), P(d)]
+        L.orc_pulse_sigma.argtypes = [P(_Params)]
+        L.orc_pulse_sigma.restype = d
+        L.orc_rotate.argtypes = [P(d), P(d)]
+        L.orc_pulse.argtypes = [P(_Params), P(d), i64]
+        L.orc_observables.argtypes = [P(_Params), P(d), P(d), P(d)]
+        L.orc_is_pulse_step.argtypes = [i64, ctypes.c_int32]
+        L.orc_pulse_number.argtypes = [i64, ctypes.c_int32]
+        L.orc_pulse_number.restype = i64
+        L.orc_run.argtypes = [P(_Params), P(d), P(d), i64, i64, ctypes.c_int, P(d), i64]
+        L.orc_run.restype = i64
+        L.orc_metropolis.argtypes = [P(_Params), P(d), P(d), u64, d, i64, i64, P(d)]
+        L.orc_metropolis.restype = i64
+        _lib = L
+    return _lib
+
+
+def _dp(a):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _state(p: Params, s) -> np.ndarray:
+    a = np.ascontiguousarray(np.asarray(s, dtype=np.float64).reshape(3, p.nz, p.ny, p.nx))
+    return a.copy()
+
+
+def _field(p: Params, h):
+    if h is None:
+        return None
+    return np.ascontiguousarray(np.asarray(h, dtype=np.float64).reshape(3, p.nz, p.ny, p.nx))
+
+
+# ---------------------------------------------------------------- Philox / noise
+def philox4x64(ctr, key) -> np.ndarray:
+    c = (ctypes.c_uint64 * 4)(*[int(v) & 0xFFFFFFFFFFFFFFFF for v in ctr])
+    k = (ctypes.c_uint64 * 2)(*[int(v) & 0xFFFFFFFFFFFFFFFF for v in key])
+    o = (ctypes.c_uint64 * 4)()
+    lib().orc_philox4x64(c, k, o)
+    return np.array(list(o), dtype=np.uint64)
+
+
+def gauss3(words) -> np.ndarray:
+    w = (ctypes.c_uint64 * 4)(*[int(v) for v in words])
+    g = (ctypes.c_double * 3)()
+    lib().orc_gauss3(w, g)
+    return np.array(list(g))
+
+
+def noise_gauss(seed: int, site: int, k: int, replica: int = 0) -> np.ndarray:
+    g = (ctypes.c_double * 3)()
+    lib().orc_noise_gauss(seed & 0xFFFFFFFFFFFFFFFF, site, k, replica, g)
+    return np.array(list(g))
+
+
+STREAM_NOISE = 0x6E6F697365
+STREAM_MC = 0x6D6F6E7465
+
+
+def pulse_sigma(p: Params) -> float:
+    return lib().orc_pulse_sigma(ctypes.byref(p.c()))
+
+
+def rotate(phi_vec, s) -> np.ndarray:
+    a = np.array(phi_vec, dtype=np.float64)
+    b = np.array(s, dtype=np.float64)
+    lib().orc_rotate(_dp(a), _dp(b))
+    return b
+
+
+def is_pulse_step(n: int, R: int) -> bool:
+    return bool(lib().orc_is_pulse_step(n, R))
+
+
+def pulse_number(n: int, R: int) -> int:
+    return int(lib().orc_pulse_number(n, R))
+
+
+# ---------------------------------------------------------------- field / rhs / step
+def heff(p: Params, s, h_site=None) -> np.ndarray:
+    a = _state(p, s)
+    out = np.empty_like(a)
+    hs = _field(p, h_site)
+    lib().orc_heff(ctypes.byref(p.c()), _dp(a), _dp(hs), _dp(out))
+    return out
+
+
+def rhs(p: Params, s, h_site=None) -> np.ndarray:
+    a = _state(p, s)
+    out = np.empty_like(a)
+    hs = _field(p, h_site)
+    lib().orc_rhs(ctypes.byref(p.c()), _dp(a), _dp(hs), _dp(out))
+    return out
+
+
+def integrate(p: Params, s, h_site=None) -> np.ndarray:
+    """One noiseless step delta t (no renormalisation, no pulse)."""
+    a = _state(p, s)
+    hs = _field(p, h_site)
+    lib().orc_integrate(ctypes.byref(p.c()), _dp(a), _dp(hs))
+    return a
+
+
+def renormalise(p: Params, s) -> np.ndarray:
+    a = _state(p, s)
+    lib().orc_renormalise(ctypes.byref(p.c()), _dp(a))
+    return a
+
+
+def pulse(p: Params, s, k: int) -> np.ndarray:
+    a = _state(p, s)
+    lib().orc_pulse(ctypes.byref(p.c()), _dp(a), k)
+    return a
+
+
+def observables(p: Params, s, h_site=None) -> np.ndarray:
+    """(M_x, M_y, M_z, E) per spin."""
+    a = _state(p, s)
+    hs = _field(p, h_site)
+    out = np.zeros(4)
+    lib().orc_observables(ctypes.byref(p.c()), _dp(a), _dp(hs), _dp(out))
+    return out
+
+
+def run(p: Params, s, nsteps: int, n0: int = 0, h_site=None, noise: bool = True):
+    """Advance nsteps from completed step n0.  Returns (state, samples) with
+    samples rows (n, M_x, M_y, M_z, E) taken after steps with n mod R == 0."""
+    a = _state(p, s)
+    hs = _field(p, h_site)
+    cap = nsteps // max(p.R, 1) + 2
+    smp = np.zeros((cap, 5))
+    ns = lib().orc_run(ctypes.byref(p.c()), _dp(a), _dp(hs), n0, nsteps, int(noise), _dp(smp), cap)
+    return a, smp[:ns]
+
+
+def metropolis(p: Params, s, nsweeps: int, mc_seed: int, R_trial=None, sweep0: int = 0, h_site=None):
+    """Sequential Metropolis sweeps.  Returns (state, series[nsweeps,4], accepted)."""
+    if R_trial is None:
+        R_trial = 1.55 * np.sqrt(p.T / (6.0 * p.J))
+    a = _state(p, s)
+    hs = _field(p, h_site)
+    ser = np.zeros((nsweeps, 4))
+    acc = lib().orc_metropolis(ctypes.byref(p.c()), _dp(a), _dp(hs), mc_seed & 0xFFFFFFFFFFFFFFFF,
+                               float(R_trial), sweep0, nsweeps, _dp(ser))
+    return a, ser, int(acc)
