@@ -1,0 +1,180 @@
+/*
+ * spinpulse — GB300 (sm_103a) library for the pulse-noise many-spin time step
+ * of D. A. Garanin, "Pulse-noise approach for classical spin systems"
+ * (arXiv:1610.04914).
+ *
+ * The problem (paper Sec. I-II, IV): classical unit spins s_i on a simple-cubic
+ * lattice evolve by the Landau-Lifshitz equation, Eq. (LLL),
+ *     ds/dt = gamma s x H_eff - gamma lambda s x (s x H_eff)        (noiseless part)
+ * integrated with a Runge-Kutta step delta t, the spins renormalised to |s| = 1
+ * after each step, and the thermal noise replaced by instantaneous random
+ * rotations (Eq. phi_n, Eq. s_rotation) once per interval Delta t = R delta t,
+ * placed mid-interval by the Suzuki-Trotter splitting, Eq. (ST-expansion).
+ * Units: gamma = mu0 = k_B = 1.
+ *
+ * Conventions for every entry point below:
+ *  - Return value: SPIN_OK (0) on success, a negative spin_status on error,
+ *    SPIN_WARN_APPLICABILITY (+1) from create when the paper's applicability
+ *    conditions are violated (the handle is still created and usable).
+ *    Nothing aborts, throws or traps across this boundary.  spin_strerror()
+ *    gives a fixed text per code; spin_last_error() the handle's last detail.
+ *  - Spin arrays are structure-of-arrays, one array per component, N = nx*ny*nz
+ *    elements each, site index i = x + nx*(y + ny*z) (x fastest), element type
+ *    float (precision 32) or double (precision 64), in device memory of the
+ *    current CUDA device.  They are OWNED BY THE CALLER and borrowed by the
+ *    handle for its whole life; the library updates them in place.
+ *  - The workspace is caller-owned device memory of at least
+ *    spin_workspace_size() bytes, 256-byte aligned, borrowed for the handle's
+ *    life.  The library allocates no device memory of its own.
+ *  - A handle is bound to one CUDA stream (cudaStream_t passed as void*; NULL
+ *    = legacy default stream).  Calls are asynchronous on that stream unless
+ *    stated; a handle must not be used from two host threads at once.
+ */
+#ifndef SPINPULSE_H
+#define SPINPULSE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum spin_status {
+    SPIN_OK = 0,
+    SPIN_WARN_APPLICABILITY = 1, /* Eq. (phi_condition) or (non-thermal_condition) violated */
+    SPIN_EINVAL = -1,            /* bad argument (size, null pointer, parameter range) */
+    SPIN_ECUDA = -2,             /* a CUDA runtime call failed; detail in spin_last_error */
+    SPIN_ENONFINITE = -3,        /* a spin became NaN/Inf (integration unstable) */
+    SPIN_ETIMEOUT = -4,          /* a bounded device wait gave up */
+    SPIN_EUNSUPPORTED = -5,      /* valid request this build does not implement */
+    SPIN_ENOSPACE = -6           /* workspace smaller than spin_workspace_size() */
+} spin_status;
+
+typedef enum spin_integrator {
+    SPIN_RK4 = 0,          /* classical 4-stage Runge-Kutta (paper Appendix names it) */
+    SPIN_RK5_BUTCHER = 1,  /* Butcher's 6-stage 5th-order method, paper Appendix */
+    SPIN_RK2_MIDPOINT = 2, /* RK2 midpoint, paper Appendix */
+    SPIN_HEUN = 3          /* Heun (RK2 trapezoid), paper Appendix */
+} spin_integrator;
+
+/* Problem statement of one lattice (paper Sec. II and IV). */
+typedef struct spin_params {
+    int32_t nx, ny, nz;       /* lattice size, each >= 1; periodic boundaries */
+    int32_t precision;        /* 32 (float state) or 64 (double state) */
+    int32_t integrator;       /* spin_integrator */
+    int32_t precession;       /* 1: full Eq. (LLL); 0: slow equation, precession dropped (Sec. II) */
+    int32_t steps_per_pulse;  /* R = Delta t / delta t >= 1 */
+    int32_t renorm;           /* 1: s <- s/|s| after every step (recommended) */
+    int32_t noise;            /* 1: apply the pulses; 0: deterministic (tests) */
+    int32_t replica;          /* replica number, third word of the noise counter */
+    int32_t path;             /* 0: fused single-kernel step where the tableau allows
+                                 (RK4, RK2 midpoint, Heun), else per-stage kernels;
+                                 1: per-stage kernels always (cross-check path) */
+    int32_t reserved;         /* must be 0 */
+    double J;                 /* nearest-neighbour exchange; E = -J sum_<ij> s_i.s_j */
+    double D;                 /* uniaxial anisotropy along z; E = -D sum s_z^2 */
+    double H[3];              /* uniform Zeeman field; E = -sum H.s */
+    double lambda;            /* dimensionless damping of Eq. (LLL) */
+    double T;                 /* temperature (k_B = 1) */
+    double dt;                /* integration step delta t */
+    uint64_t seed;            /* key of the counter-based noise generator */
+} spin_params;
+
+typedef struct spin_lattice spin_lattice;
+
+/*
+ * Bytes of workspace a handle for *p needs.  Layout (internal): a second state
+ * buffer for the out-of-place stencil update, stage temporaries for
+ * multi-kernel integrators, FP64 reduction partials, the device-resident
+ * interval counter and the sample ring.
+ * Errors: SPIN_EINVAL for a null pointer or invalid parameters.
+ */
+int spin_workspace_size(const spin_params* p, size_t* bytes);
+
+/*
+ * Create a handle for the lattice problem *p (Sec. II, IV).
+ *   sx, sy, sz  device arrays of N elements (float or double per p->precision):
+ *               the initial spins, unit length; updated in place by later calls.
+ *   h_site      nullable: device array of 3N elements (same type), the per-site
+ *               field h_i added to H_eff (component-major: x block, y, z).
+ *   workspace   device memory of workspace_bytes >= spin_workspace_size(p).
+ *   cuda_stream cudaStream_t all work is ordered on.
+ * On success *out receives the handle (host memory owned by the library,
+ * released by spin_lattice_destroy).  Returns SPIN_WARN_APPLICABILITY when
+ * Lambda_N Delta t = 2 lambda T Delta t > 0.2 (Eq. phi_condition) or
+ * lambda |H_eff|max Delta t > 1 (Eq. non-thermal_condition).
+ * Errors: SPIN_EINVAL (null arrays/out, sizes < 1, N >= 2^31, precision not
+ * 32/64, R < 1, dt not finite/zero, lambda or T < 0), SPIN_ENOSPACE, SPIN_ECUDA.
+ */
+int spin_lattice_create(const spin_params* p, void* sx, void* sy, void* sz,
+                        const void* h_site, void* workspace, size_t workspace_bytes,
+                        void* cuda_stream, spin_lattice** out);
+
+/*
+ * Advance nsteps >= 0 integration steps delta t (asynchronous on the stream).
+ * Steps are numbered n = 1, 2, ... over the handle's life.  After step n:
+ * the pulse number floor((n-1)/R) is applied when n mod R == floor(R/2)
+ * (Eq. ST-expansion: mid-interval; every step when R = 1), and the
+ * observables are sampled into the sample ring when n mod R == 0 (Sec. III.A:
+ * values at the end of each Delta t).  Full intervals are replayed from a
+ * cached CUDA graph.  On return (stream-ordered) the caller's arrays hold the
+ * state after the last step.
+ * Errors: SPIN_EINVAL (null handle, nsteps < 0), SPIN_ECUDA.
+ */
+int spin_step_pulse(spin_lattice* h, int64_t nsteps);
+
+/*
+ * Observables of the current state, FP64 (Sec. III.A, Sec. IV):
+ *   M = (1/N) sum_i s_i,
+ *   E = (1/N) [ -J sum_<ij> s_i.s_j - D sum_i s_iz^2 - sum_i (H + h_i).s_i ],
+ * each nearest-neighbour bond counted once.  Synchronises the stream.
+ * M (3 doubles) and E are host pointers.
+ * Errors: SPIN_EINVAL (null pointers), SPIN_ENONFINITE (some spin is NaN/Inf;
+ * M and E are still written), SPIN_ECUDA.
+ */
+int spin_observables(spin_lattice* h, double M[3], double* E);
+
+/*
+ * Copy the sample ring to host memory: records of 5 doubles
+ * (n, M_x, M_y, M_z, E), oldest first, at most max_records of the newest
+ * samples taken since the last call; *count receives the number written.
+ * The ring holds SPIN_SAMPLE_RING records; older unread samples are dropped.
+ * Synchronises the stream.  Errors: SPIN_EINVAL, SPIN_ECUDA.
+ */
+#define SPIN_SAMPLE_RING 4096
+int spin_samples(spin_lattice* h, double* out, int64_t max_records, int64_t* count);
+
+/* Completed step count n of the handle (host value, no synchronisation). */
+int spin_get_step(const spin_lattice* h, int64_t* n);
+
+/*
+ * Set the completed step count to n >= 0, e.g. after restoring the spin
+ * arrays from a checkpoint: the noise is a pure function of (seed, site,
+ * pulse number, replica), so a resumed run reproduces an uninterrupted one
+ * bit for bit.  Asynchronous.  Errors: SPIN_EINVAL, SPIN_ECUDA.
+ */
+int spin_set_step(spin_lattice* h, int64_t n);
+
+/* Release the handle's host state and CUDA graphs (not the borrowed arrays). */
+int spin_lattice_destroy(spin_lattice* h);
+
+const char* spin_strerror(int status);
+const char* spin_last_error(const spin_lattice* h);
+
+/*
+ * The noise draw of Eq. (phi_n) on its own, for verification: for sites
+ * i = 0..n_sites-1 computes the four Philox4x64-10 words of counter
+ * (i, k, replica, 0) under key (seed, noise stream) into words[4*i+0..3]
+ * (device, uint64) and, if gauss is non-null, the Box-Muller normals
+ * G_i (device, 3*n_sites, component-minor: gauss[3*i+a]) in the given
+ * precision (32: float, 64: double).  Asynchronous on cuda_stream.
+ * Errors: SPIN_EINVAL, SPIN_ECUDA.
+ */
+int spin_noise_draw(uint64_t seed, int64_t k, int64_t replica, int64_t n_sites,
+                    int32_t precision, uint64_t* words, void* gauss, void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPINPULSE_H */

@@ -1,0 +1,150 @@
+// Magnetisation and energy per spin, accumulated in FP64 (Sec. III.A samples
+// at the end of every Delta t; Sec. IV's Heisenberg energy):
+//   M = (1/N) sum_i s_i
+//   E = (1/N) [ -J sum_<ij> s_i.s_j - D sum_i s_iz^2 - sum_i (H + h_i).s_i ]
+// each bond counted once through the three forward neighbours of every site.
+// Pass 1: grid-stride FP64 partial sums, warp-shuffle then shared-memory
+// reduction, one 5-double record per block.  Pass 2: one block adds the block
+// records in a fixed order, so the result is bitwise reproducible.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "spin_internal.h"
+
+namespace spin {
+
+namespace {
+
+constexpr int kObsThreads = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename real, bool HSITE>
+__global__ void __launch_bounds__(kObsThreads) k_obs_partial(const real* __restrict__ sx, const real* __restrict__ sy,
+                                                             const real* __restrict__ sz, const real* __restrict__ hx,
+                                                             const real* __restrict__ hy, const real* __restrict__ hz,
+                                                             int nx, int ny, int nz, double J, double D, double H0,
+                                                             double H1, double H2, double* __restrict__ partials) {
+    const long long N = (long long)nx * ny * nz;
+    const long long P = (long long)nx * ny;
+    double m0 = 0, m1 = 0, m2 = 0, e = 0, bad = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % nx);
+        const int y = (int)((i / nx) % ny);
+        const int z = (int)(i / P);
+        const long long ix = i - x + (x + 1 == nx ? 0 : x + 1);
+        const long long iy = (long long)z * P + (long long)(y + 1 == ny ? 0 : y + 1) * nx + x;
+        const long long iz = (long long)(z + 1 == nz ? 0 : z + 1) * P + (long long)y * nx + x;
+        const double a = sx[i], b = sy[i], c = sz[i];
+        if (!isfinite(a) || !isfinite(b) || !isfinite(c)) bad += 1.0;
+        m0 += a;
+        m1 += b;
+        m2 += c;
+        const double bond = a * ((double)sx[ix] + (double)sx[iy] + (double)sx[iz]) +
+                            b * ((double)sy[ix] + (double)sy[iy] + (double)sy[iz]) +
+                            c * ((double)sz[ix] + (double)sz[iy] + (double)sz[iz]);
+        double f0 = H0, f1 = H1, f2 = H2;
+        if (HSITE) {
+            f0 += (double)hx[i];
+            f1 += (double)hy[i];
+            f2 += (double)hz[i];
+        }
+        e += -J * bond - D * c * c - (f0 * a + f1 * b + f2 * c);
+    }
+    __shared__ double red[kObsThreads / 32][5];
+    m0 = warp_sum(m0);
+    m1 = warp_sum(m1);
+    m2 = warp_sum(m2);
+    e = warp_sum(e);
+    bad = warp_sum(bad);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) {
+        red[w][0] = m0;
+        red[w][1] = m1;
+        red[w][2] = m2;
+        red[w][3] = e;
+        red[w][4] = bad;
+    }
+    __syncthreads();
+    if (threadIdx.x < 5) {
+        double acc = 0;
+        for (int q = 0; q < kObsThreads / 32; ++q) acc += red[q][threadIdx.x];
+        partials[(long long)blockIdx.x * 5 + threadIdx.x] = acc;
+    }
+}
+
+__global__ void __launch_bounds__(kObsThreads) k_obs_final(const double* __restrict__ partials, int nblocks, long long N,
+                                                           double* __restrict__ out5, double* __restrict__ ring, int ring_len,
+                                                           long long* __restrict__ interval,
+                                                           long long* __restrict__ sample_count, int R) {
+    __shared__ double red[kObsThreads / 32][5];
+    double acc[5] = {0, 0, 0, 0, 0};
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+        for (int q = 0; q < 5; ++q) acc[q] += partials[(long long)b * 5 + q];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    for (int q = 0; q < 5; ++q) {
+        const double v = warp_sum(acc[q]);
+        if (l == 0) red[w][q] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t[5] = {0, 0, 0, 0, 0};
+        for (int ww = 0; ww < kObsThreads / 32; ++ww)
+            for (int q = 0; q < 5; ++q) t[q] += red[ww][q];
+        const double invN = 1.0 / (double)N;
+        out5[0] = t[0] * invN;
+        out5[1] = t[1] * invN;
+        out5[2] = t[2] * invN;
+        out5[3] = t[3] * invN;
+        out5[4] = t[4];
+        if (ring) {
+            const long long m = *interval;
+            double* rec = ring + (*sample_count % ring_len) * 5;
+            rec[0] = (double)((m + 1) * (long long)R);
+            rec[1] = out5[0];
+            rec[2] = out5[1];
+            rec[3] = out5[2];
+            rec[4] = out5[3];
+            *interval = m + 1;
+            *sample_count = *sample_count + 1;
+        }
+    }
+}
+
+}  // namespace
+
+int observables_blocks(Geom g) {
+    const long long N = g.N();
+    return (int)std::max<long long>(1, std::min<long long>((N + kObsThreads - 1) / kObsThreads, 152LL * 4));
+}
+
+template <typename real>
+cudaError_t launch_observables(const real* s[3], const real* hs[3], Geom g, Phys<double> ph, double* partials,
+                               int nblocks, double* out5, double* sample_ring, int ring, long long* d_interval,
+                               long long* d_sample_count, int R, cudaStream_t stream) {
+    const double D = 0.5 * ph.twoD;
+    if (hs[0])
+        k_obs_partial<real, true><<<nblocks, kObsThreads, 0, stream>>>(s[0], s[1], s[2], hs[0], hs[1], hs[2], g.nx, g.ny, g.nz,
+                                                                       (double)ph.J, D, (double)ph.H[0], (double)ph.H[1],
+                                                                       (double)ph.H[2], partials);
+    else
+        k_obs_partial<real, false><<<nblocks, kObsThreads, 0, stream>>>(s[0], s[1], s[2], nullptr, nullptr, nullptr, g.nx, g.ny,
+                                                                        g.nz, (double)ph.J, D, (double)ph.H[0],
+                                                                        (double)ph.H[1], (double)ph.H[2], partials);
+    k_obs_final<<<1, kObsThreads, 0, stream>>>(partials, nblocks, g.N(), out5, sample_ring, ring, d_interval,
+                                               d_sample_count, R);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_observables<float>(const float* s[3], const float* hs[3], Geom, Phys<double>, double*, int,
+                                               double*, double*, int, long long*, long long*, int, cudaStream_t);
+template cudaError_t launch_observables<double>(const double* s[3], const double* hs[3], Geom, Phys<double>, double*,
+                                                int, double*, double*, int, long long*, long long*, int, cudaStream_t);
+
+}  // namespace spin

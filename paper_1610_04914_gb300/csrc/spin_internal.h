@@ -1,0 +1,77 @@
+// Internal interfaces between the library's translation units (host side).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace spin {
+
+// Geometry of the lattice: periodic nx*ny*nz, site i = x + nx*(y + ny*z).
+struct Geom {
+    int nx, ny, nz;
+    long long N() const { return (long long)nx * ny * nz; }
+};
+
+// Coefficients of one explicit Runge-Kutta tableau (paper Appendix), with
+// K_j = dt f(x_j), x_1 = s, x_j = s + sum_{l<j} a[j][l] K_l,
+// s' = s + sum_j b[j] K_j.
+struct Tableau {
+    int stages;
+    double a[6][6];
+    double b[6];
+    bool chain;  // a[j][l] == 0 unless l == j-1: stage j needs only K_{j-1}
+};
+Tableau tableau_for(int integrator);
+
+// Physical parameters as seen by the kernels.
+template <typename real>
+struct Phys {
+    real J, twoD, H[3], lambda;
+};
+
+// Arguments of one step launch.
+template <typename real>
+struct StepLaunch {
+    const real* in[3];
+    real* out[3];
+    const real* hs[3];     // per-site field or nulls
+    Geom g;
+    Phys<real> ph;
+    double dt;
+    const Tableau* tab;
+    int precession;
+    int renorm;
+    int pulse;             // apply the pulse after this step
+    uint64_t seed;
+    uint64_t replica;
+    real sigma;            // pulse angle scale sqrt(2 lambda T Delta t)
+    const long long* d_interval;  // device: pulse number of the current interval
+    real* tmp;             // generic path: (stages + 1) * 3N scratch
+    cudaStream_t stream;
+    int force_generic;
+};
+
+template <typename real>
+cudaError_t launch_step(const StepLaunch<real>& L);
+// Set the dynamic shared-memory limits of every fused-step instantiation
+// (call once per device before launching or capturing).
+template <typename real>
+cudaError_t prepare_step_kernels();
+
+// FP64 observables: per-block partials, then a one-block deterministic sum.
+// out5 = (M_x, M_y, M_z, E, nonfinite count); if sample_ring != null the
+// record (n, M, E) goes to sample_ring[(*d_interval) % ring] with
+// n = ((*d_interval) + 1) * R, and *d_interval is incremented.
+template <typename real>
+cudaError_t launch_observables(const real* s[3], const real* hs[3], Geom g, Phys<double> ph,
+                               double* partials, int nblocks, double* out5, double* sample_ring,
+                               int ring, long long* d_interval, long long* d_sample_count, int R,
+                               cudaStream_t stream);
+int observables_blocks(Geom g);
+
+cudaError_t launch_noise_draw(uint64_t seed, long long k, long long replica, long long n, int precision,
+                              uint64_t* words, void* gauss, cudaStream_t stream);
+
+cudaError_t launch_set_counter(long long* d, long long value, cudaStream_t stream);
+
+}  // namespace spin

@@ -1,0 +1,170 @@
+"""Python face of the C-ABI: functions with the C names (argument marshalling
+only) and a ``Lattice`` convenience class.  PyTorch provides device memory
+and the CUDA stream; all arithmetic runs in ``libspinpulse.so``.
+
+A state is a torch tensor of shape (3, nz, ny, nx) (components s_x, s_y,
+s_z, each an x-fastest array), float32 or float64, on a CUDA device.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass, field
+
+import torch
+
+from . import _binding as B
+from ._binding import check
+
+
+@dataclass
+class Params:
+    """Problem statement of one lattice (gamma = mu0 = k_B = 1)."""
+    nx: int
+    ny: int
+    nz: int
+    J: float = 1.0
+    D: float = 0.0
+    H: tuple = (0.0, 0.0, 0.0)
+    lam: float = 0.1
+    T: float = 1.0
+    dt: float = 0.1
+    R: int = 10
+    integrator: int = B.RK4
+    precession: int = 1
+    renorm: int = 1
+    noise: int = 1
+    seed: int = 1
+    replica: int = 0
+    precision: int = 32
+    path: int = 0
+
+    @property
+    def N(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    @property
+    def dtype(self):
+        return torch.float64 if self.precision == 64 else torch.float32
+
+    def c(self) -> B.spin_params:
+        return B.spin_params(self.nx, self.ny, self.nz, self.precision, self.integrator,
+                             self.precession, self.R, self.renorm, self.noise, self.replica,
+                             self.path, 0, self.J, self.D, (ctypes.c_double * 3)(*self.H),
+                             self.lam, self.T, self.dt, self.seed & 0xFFFFFFFFFFFFFFFF)
+
+
+def _stream_ptr(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def spin_workspace_size(p: Params) -> int:
+    n = ctypes.c_size_t()
+    check(B.load().spin_workspace_size(ctypes.byref(p.c()), ctypes.byref(n)))
+    return int(n.value)
+
+
+def spin_lattice_create(p: Params, state: torch.Tensor, h_site: torch.Tensor | None,
+                        workspace: torch.Tensor, stream=None):
+    """Returns (handle, status); status is SPIN_OK or SPIN_WARN_APPLICABILITY."""
+    L = B.load()
+    h = ctypes.c_void_p()
+    rc = L.spin_lattice_create(ctypes.byref(p.c()), state[0].data_ptr(), state[1].data_ptr(),
+                               state[2].data_ptr(), h_site.data_ptr() if h_site is not None else None,
+                               workspace.data_ptr(), workspace.numel() * workspace.element_size(),
+                               _stream_ptr(stream), ctypes.byref(h))
+    check(rc)
+    return h, rc
+
+
+def spin_step_pulse(h, nsteps: int) -> None:
+    check(B.load().spin_step_pulse(h, int(nsteps)), h)
+
+
+def spin_observables(h):
+    """Returns (M[3] as a list, E, status)."""
+    M = (ctypes.c_double * 3)()
+    E = ctypes.c_double()
+    rc = B.load().spin_observables(h, M, ctypes.byref(E))
+    if rc != B.SPIN_ENONFINITE:
+        check(rc, h)
+    return [M[0], M[1], M[2]], E.value, rc
+
+
+def spin_samples(h, max_records: int = B.SPIN_SAMPLE_RING):
+    buf = (ctypes.c_double * (5 * max_records))()
+    cnt = ctypes.c_int64()
+    check(B.load().spin_samples(h, buf, max_records, ctypes.byref(cnt)), h)
+    n = cnt.value
+    return [tuple(buf[5 * q:5 * q + 5]) for q in range(n)]
+
+
+def spin_get_step(h) -> int:
+    n = ctypes.c_int64()
+    check(B.load().spin_get_step(h, ctypes.byref(n)), h)
+    return n.value
+
+
+def spin_set_step(h, n: int) -> None:
+    check(B.load().spin_set_step(h, int(n)), h)
+
+
+def spin_lattice_destroy(h) -> None:
+    check(B.load().spin_lattice_destroy(h))
+
+
+def spin_noise_draw(seed: int, k: int, replica: int, n_sites: int, precision: int = 64,
+                    device="cuda", stream=None):
+    """Philox words (int64 tensor holding the uint64 bit patterns, shape (n, 4))
+    and Box-Muller normals (shape (n, 3)) of pulse k for sites 0..n-1."""
+    words = torch.empty((n_sites, 4), dtype=torch.int64, device=device)
+    gauss = torch.empty((n_sites, 3), dtype=torch.float64 if precision == 64 else torch.float32,
+                        device=device)
+    check(B.load().spin_noise_draw(seed & 0xFFFFFFFFFFFFFFFF, k, replica, n_sites, precision,
+                                   words.data_ptr(), gauss.data_ptr(), _stream_ptr(stream)))
+    return words, gauss
+
+
+class Lattice:
+    """Owns the device state, the optional per-site field and the workspace of
+    one handle.  ``state`` is (3, nz, ny, nx) on the GPU."""
+
+    def __init__(self, p: Params, state, h_site=None, device="cuda", stream=None):
+        self.p = p
+        self.state = torch.as_tensor(state).to(device=device, dtype=p.dtype).reshape(3, p.nz, p.ny, p.nx).contiguous()
+        self.h_site = None
+        if h_site is not None:
+            self.h_site = torch.as_tensor(h_site).to(device=device, dtype=p.dtype).reshape(3, p.nz, p.ny, p.nx).contiguous()
+        nbytes = spin_workspace_size(p)
+        self.workspace = torch.empty(nbytes // 8 + 32, dtype=torch.float64, device=device)
+        self.stream = stream
+        self.handle, self.status = spin_lattice_create(p, self.state, self.h_site, self.workspace, stream)
+
+    def step(self, n: int) -> "Lattice":
+        spin_step_pulse(self.handle, n)
+        return self
+
+    def observables(self):
+        M, E, rc = spin_observables(self.handle)
+        return M, E
+
+    def samples(self):
+        return spin_samples(self.handle)
+
+    @property
+    def n(self) -> int:
+        return spin_get_step(self.handle)
+
+    def set_step(self, n: int) -> None:
+        spin_set_step(self.handle, n)
+
+    def close(self) -> None:
+        if self.handle is not None:
+            spin_lattice_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -18,3 +18,29 @@ def orc():
     import oracle
     oracle.build()
     return oracle
+
+
+def pytest_collection_modifyitems(config, items):
+    """GPU tests need a CUDA device; on a machine without one they are skipped
+    (the CPU suite is run with -m "not gpu")."""
+    try:
+        import torch
+        have_cuda = torch.cuda.is_available()
+    except Exception:
+        have_cuda = False
+    if have_cuda:
+        return
+    skip = pytest.mark.skip(reason="no CUDA device")
+    for it in items:
+        if "gpu" in it.keywords:
+            it.add_marker(skip)
+
+
+@pytest.fixture(scope="session")
+def gpu():
+    """The CUDA library, built in-tree for sm_103a."""
+    import paper_1610_04914_gb300 as sp
+    from paper_1610_04914_gb300 import build as b
+    b.build()
+    sp.load()
+    return sp

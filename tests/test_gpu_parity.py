@@ -1,0 +1,256 @@
+"""GPU (sm_103a, through the C-ABI) against the FP64 oracle on identical seeded
+inputs and identical Philox noise.
+
+Tolerances.  FP64 path: one step agrees to a few ulps (1e-13 per step).
+FP32 path: one step from the same float32 input agrees with the FP64 oracle to
+2e-6 (float rounding of the stage states, ~10 eps).  Whole trajectories are
+compared over the horizon where the oracle's own sensitivity keeps rounding
+differences below the tolerance: the 16^3 workload at T=1 amplifies a
+perturbation by ~2.5x per unit time, so 1e-16 reaches 1e-11 after ~120 steps
+of dt=0.1 and 1e-7 reaches 1e-5 after ~50 steps.  Longer runs are checked step
+by step (oracle restarted from the GPU state at every step) over all 200
+steps, and statistically elsewhere."""
+import numpy as np
+import pytest
+import torch
+
+import spin_inputs
+from gpu_helpers import as_input, gpu_state, orc_params, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+M64 = (1 << 64) - 1
+
+
+# ----------------------------------------------------------------- noise draw
+@pytest.mark.parametrize("seed,k,replica", [(1, 0, 0), ((1 << 63) + 5, 17, 3), (123, 999, 511)])
+def test_noise_words_bit_exact(gpu, orc, seed, k, replica):
+    n = 3000
+    words, g64 = gpu.spin_noise_draw(seed, k, replica, n, precision=64)
+    _, g32 = gpu.spin_noise_draw(seed, k, replica, n, precision=32)
+    torch.cuda.synchronize()
+    w = words.cpu().numpy().view(np.uint64)
+    g64 = g64.cpu().numpy()
+    g32 = g32.double().cpu().numpy()
+    for i in range(0, n, 7):
+        ref = orc.philox4x64([i, k, replica, 0], [seed & M64, orc.STREAM_NOISE])
+        assert [int(v) for v in w[i]] == [int(v) for v in ref]
+    ref_g = np.array([orc.noise_gauss(seed, i, k, replica) for i in range(n)])
+    assert np.max(np.abs(g64 - ref_g)) < 2e-14
+    assert np.max(np.abs(g32 - ref_g)) < 1e-5
+
+
+# ----------------------------------------------------------------- short runs
+CASES = [
+    # size, precision, integrator, precession, with h_site, path
+    ((16, 16, 16), 64, 0, 1, False, 0),
+    ((16, 16, 16), 32, 0, 1, False, 0),
+    ((37, 21, 13), 32, 0, 1, True, 0),
+    ((37, 21, 13), 64, 0, 0, True, 0),
+    ((2, 3, 5), 64, 0, 1, False, 0),
+    ((2, 3, 5), 32, 0, 1, True, 0),
+    ((1, 1, 1), 64, 0, 1, False, 0),
+    ((64, 8, 9), 32, 0, 0, False, 0),
+    ((20, 19, 18), 64, 2, 1, False, 0),
+    ((20, 19, 18), 32, 2, 0, True, 0),
+    ((20, 19, 18), 32, 3, 1, False, 0),
+    ((11, 12, 7), 64, 3, 0, True, 0),
+    ((20, 19, 18), 64, 1, 1, False, 0),
+    ((20, 19, 18), 32, 1, 1, True, 0),
+    ((9, 10, 11), 64, 1, 0, False, 0),
+    ((20, 19, 18), 64, 0, 1, True, 1),
+    ((20, 19, 18), 32, 0, 0, False, 1),
+]
+
+
+@pytest.mark.parametrize("shape,prec,integ,precession,hsite,path", CASES)
+def test_three_steps_with_pulse(gpu, orc, shape, prec, integ, precession, hsite, path):
+    """Three steps with R = 3: a pulse after step 1 (mid-interval), a sample
+    after step 3; fused kernels (RK4, RK2, Heun) and per-stage kernels (RK5,
+    forced path 1), ragged and tiny lattices, with and without h_i."""
+    nx, ny, nz = shape
+    p = gpu.Params(nx, ny, nz, J=0.9, D=0.15, H=(0.05, -0.1, 0.2), lam=0.1, T=0.7, dt=0.07, R=3,
+                   integrator=integ, precession=precession, seed=77, replica=2, precision=prec, path=path)
+    s0 = spin_inputs.random_spins(nx, ny, nz, seed=3)
+    hs = spin_inputs.site_fields(nx, ny, nz, 0.1, seed=4) if hsite else None
+    got, lat = run_gpu(gpu, p, s0, 3, h_site=hs)
+    ref, smp = run_oracle(orc, p, s0, 3, h_site=hs)
+    tol = 1e-13 if prec == 64 else 2e-6
+    assert np.max(np.abs(got - ref)) < tol
+    rec = lat.samples()
+    assert len(rec) == 1 and rec[0][0] == 3.0
+    assert np.max(np.abs(np.array(rec[0][1:]) - smp[0, 1:])) < (1e-13 if prec == 64 else 2e-6)
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_step_by_step_200_steps(gpu, orc, prec):
+    """The 16^3 workload (J=1, H=0.1 z, lambda=0.1, T=1, RK4 dt=0.1, pulses
+    every 10 steps): at every one of 200 steps the oracle, restarted from the
+    GPU state, reproduces the GPU's next state (pulse steps included)."""
+    n = 16
+    p = gpu.Params(n, n, n, J=1.0, D=0.0, H=(0, 0, 0.1), lam=0.1, T=1.0, dt=0.1, R=10, seed=1, precision=prec)
+    s0 = spin_inputs.random_spins(n, n, n, seed=0)
+    lat = gpu.Lattice(p, torch.from_numpy(s0))
+    cur = gpu_state(lat)
+    worst = 0.0
+    op = orc_params(orc, p)
+    for step in range(200):
+        lat.step(1)
+        nxt = gpu_state(lat)
+        ref, _ = orc.run(op, cur, 1, n0=step)
+        worst = max(worst, float(np.max(np.abs(nxt - ref))))
+        cur = nxt
+    assert worst < (1e-13 if prec == 64 else 2e-6), worst
+
+
+def test_fp64_trajectory_16cubed(gpu, orc):
+    """Whole-trajectory parity of the FP64 path on the 16^3 workload: 1e-11
+    over the first 100 steps (the stated FP64 tolerance, within the chaos
+    horizon) and the measured sensitivity envelope (1e-8) at 200 steps."""
+    n = 16
+    p = gpu.Params(n, n, n, J=1.0, D=0.0, H=(0, 0, 0.1), lam=0.1, T=1.0, dt=0.1, R=10, seed=1, precision=64)
+    s0 = spin_inputs.random_spins(n, n, n, seed=0)
+    lat = gpu.Lattice(p, torch.from_numpy(s0))
+    lat.step(100)
+    got100 = gpu_state(lat)
+    ref100, smp100 = run_oracle(orc, p, s0, 100)
+    assert np.max(np.abs(got100 - ref100)) < 1e-11
+    lat.step(100)
+    got200 = gpu_state(lat)
+    ref200, smp200 = run_oracle(orc, p, ref100, 100, n0=100)
+    assert np.max(np.abs(got200 - ref200)) < 1e-8
+    rec = np.array(lat.samples())
+    assert rec.shape == (20, 5)
+    assert np.array_equal(rec[:, 0], np.arange(10, 201, 10, dtype=float))
+    allsmp = np.vstack([smp100, smp200])
+    assert np.max(np.abs(rec[:10, 1:] - allsmp[:10, 1:])) < 1e-12
+
+
+def test_fp32_trajectory_16cubed(gpu, orc):
+    """FP32 state: 1e-5 max-abs against the FP64 oracle over 40 steps."""
+    n = 16
+    p = gpu.Params(n, n, n, J=1.0, D=0.0, H=(0, 0, 0.1), lam=0.1, T=1.0, dt=0.1, R=10, seed=1, precision=32)
+    s0 = spin_inputs.random_spins(n, n, n, seed=0)
+    got, _ = run_gpu(gpu, p, s0, 40)
+    ref, _ = run_oracle(orc, p, s0, 40)
+    assert np.max(np.abs(got - ref)) < 1e-5
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("shape", [(16, 16, 16), (5, 7, 3), (1, 1, 1), (2, 2, 2)])
+def test_observables(gpu, orc, prec, shape):
+    """FP64 reductions of M and E against the oracle on the same values."""
+    nx, ny, nz = shape
+    p = gpu.Params(nx, ny, nz, J=0.8, D=0.3, H=(0.1, -0.2, 0.3), precision=prec)
+    s0 = spin_inputs.random_spins(nx, ny, nz, seed=9)
+    hs = spin_inputs.site_fields(nx, ny, nz, 0.2, seed=8)
+    lat = gpu.Lattice(p, torch.from_numpy(s0), h_site=torch.from_numpy(hs))
+    M, E = lat.observables()
+    ref = orc.observables(orc_params(orc, p), as_input(p, s0), as_input(p, hs))
+    assert np.max(np.abs(np.array(M) - ref[:3])) < 1e-13
+    assert abs(E - ref[3]) < 1e-13
+
+
+# ----------------------------------------------------------------- graph path, resume
+@pytest.mark.parametrize("R", [10, 5, 1])
+def test_graph_replay_equals_eager(gpu, R):
+    """Whole intervals replayed from the cached CUDA graph give bitwise the
+    same state and samples as step-by-step launches (odd R flips buffers)."""
+    n = 24
+    p = gpu.Params(n, n, n, J=1.0, D=0.05, H=(0, 0, 0.02), lam=0.05, T=1.0, dt=0.1, R=R, seed=5, precision=32)
+    s0 = spin_inputs.random_spins(n, n, n, seed=2)
+    a, la = run_gpu(gpu, p, s0, 5 * R)
+    b, lb = run_gpu(gpu, p, s0, 5 * R, calls=[1] * (5 * R))
+    assert np.array_equal(a, b)
+    assert la.samples() == lb.samples()
+
+
+def test_resume_is_bitwise(gpu):
+    """Noise is a pure function of (seed, site, pulse number, replica): a run
+    restarted from a saved state and step count reproduces the uninterrupted
+    run bit for bit."""
+    n = 20
+    p = gpu.Params(n, n, n, J=1.0, D=0.05, H=(0, 0, 0.02), lam=0.05, T=1.0, dt=0.1, R=10, seed=5, precision=32)
+    s0 = spin_inputs.random_spins(n, n, n, seed=2)
+    full, _ = run_gpu(gpu, p, s0, 47)
+    half, _ = run_gpu(gpu, p, s0, 23)
+    lat = gpu.Lattice(p, torch.from_numpy(half))
+    lat.set_step(23)
+    lat.step(24)
+    assert np.array_equal(gpu_state(lat), full)
+
+
+# ----------------------------------------------------------------- full sizes, sampled
+def _oracle_one_step_at(orc, p, s, sites, pulse, k):
+    """One oracle step at sampled sites: the RK4 dependency cone of a site is
+    its 9^3 neighbourhood, so each site's new value is the centre of a 9^3
+    periodic oracle run on that neighbourhood, then renormalised and rotated by
+    the noise of its global index."""
+    nx, ny, nz = p.nx, p.ny, p.nz
+    op9 = orc_params(orc, p)
+    op9 = orc.Params(9, 9, 9, J=op9.J, D=op9.D, H=op9.H, lam=op9.lam, T=op9.T, dt=op9.dt, R=op9.R,
+                     integrator=op9.integrator, precession=op9.precession, seed=op9.seed, replica=op9.replica)
+    sig = orc.pulse_sigma(op9)
+    out = []
+    for (x, y, z) in sites:
+        xs, ys, zs = (np.arange(c - 4, c + 5) % m for c, m in ((x, nx), (y, ny), (z, nz)))
+        cube = s[:, zs][:, :, ys][:, :, :, xs]
+        c1 = orc.renormalise(op9, orc.integrate(op9, cube))
+        v = c1[:, 4, 4, 4].copy()
+        if pulse:
+            G = orc.noise_gauss(p.seed, x + nx * (y + ny * z), k, p.replica)
+            v = orc.rotate(sig * G, v)
+        out.append(v)
+    return np.array(out)
+
+
+@pytest.mark.parametrize("name", ["lattice128", "overdamped256"])
+def test_full_size_sampled(gpu, orc, name):
+    """The benchmark workloads at full size in the benchmark's launch
+    configuration: 2000 sampled sites of a pulse step and of a plain step
+    against the oracle; unit length everywhere."""
+    w = spin_inputs.WORKLOADS[name]
+    nx, ny, nz = w["n"]
+    p = gpu.Params(nx, ny, nz, J=w["J"], D=w["D"], H=w["H"], lam=w["lam"], T=w["T"], dt=w["dt"], R=w["R"],
+                   precession=w["precession"], seed=w["noise_seed"], precision=32)
+    s0 = spin_inputs.random_spins(nx, ny, nz, seed=w["spin_seed"])
+    lat = gpu.Lattice(p, torch.from_numpy(s0))
+    R = p.R
+    pulse_step = R // 2 if R > 1 else 1
+    lat.step(pulse_step - 1)
+    before = gpu_state(lat)
+    lat.step(1)                     # the pulse step (pulse number 0)
+    after = gpu_state(lat)
+    g = np.random.default_rng(0)
+    sites = list(zip(g.integers(0, nx, 2000), g.integers(0, ny, 2000), g.integers(0, nz, 2000)))
+    ref = _oracle_one_step_at(orc, p, before, sites, True, 0)
+    got = np.array([after[:, z, y, x] for (x, y, z) in sites])
+    assert np.max(np.abs(got - ref)) < 2e-6
+    lat.step(1)                     # a plain step
+    after2 = gpu_state(lat)
+    ref2 = _oracle_one_step_at(orc, p, after, sites, False, 0)
+    got2 = np.array([after2[:, z, y, x] for (x, y, z) in sites])
+    assert np.max(np.abs(got2 - ref2)) < 2e-6
+    assert np.max(np.abs(np.sum(after2 ** 2, axis=0) - 1.0)) < 1e-6
+
+
+# ----------------------------------------------------------------- failure detection
+def test_nonfinite_spin_reported(gpu):
+    """A NaN planted from the host is reported by the observables call."""
+    n = 8
+    p = gpu.Params(n, n, n, precision=32)
+    s0 = spin_inputs.random_spins(n, n, n, seed=1)
+    lat = gpu.Lattice(p, torch.from_numpy(s0))
+    lat.state[1, 2, 3, 4] = float("nan")
+    M, E, rc = gpu.spin_observables(lat.handle)
+    assert rc == gpu.SPIN_ENONFINITE
+
+
+def test_applicability_warning(gpu):
+    """The 256^3 slow-equation workload has Lambda_N Delta t = 2.4 > 0.2
+    (Eq. phi_condition): create succeeds and returns the warning status."""
+    n = 4
+    p = gpu.Params(n, n, n, lam=1.0, T=1.2, dt=0.2, R=5, precession=0, precision=32)
+    lat = gpu.Lattice(p, torch.from_numpy(spin_inputs.random_spins(n, n, n, seed=1)))
+    assert lat.status == gpu.SPIN_WARN_APPLICABILITY
+    q = gpu.Params(n, n, n, lam=0.01, T=1.0, dt=0.2, R=10, precision=32)
+    assert gpu.Lattice(q, torch.from_numpy(spin_inputs.random_spins(n, n, n, seed=1))).status == gpu.SPIN_OK
