@@ -1,0 +1,391 @@
+"""Benchmark of the pulse-noise lattice step (arXiv:1610.04914) on GB300.
+
+One bench step = one noise interval of the 128^3 workload: R = 10 fused RK4
+steps delta t = 0.2 of the FP32 state, the noise pulse after step 5, the FP64
+sample of M and E after step 10 (J=1, D=0.05 along z, H=(0,0,0.02),
+lambda=0.01, T=1.0, random spins seed 2), replayed from the library's CUDA
+graph through the C-ABI.  L2 is flushed (256 MiB write) before every timed
+step; the 10 steps inside one interval see the L2-resident 50 MB working set,
+as a real run does.
+
+Prints one JSON line (see the keys below).  ``--impl reference`` times the
+FP64 CPU oracle on the same workload instead (bounded samples per step).
+Multi-GPU: independent replicas, one per rank (the path has no exchange).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import spin_inputs  # noqa: E402
+
+WORKLOAD = "lattice128"
+T_BENCH = 1.0
+FALLBACK_HBM_GBS = 6800.0
+SMS, FP32_LANES, MAX_SM_MHZ = 152, 128, 2070.0
+# algorithmic FP32 flops of one RK4 spin-step (FMA = 2): 4 x (stencil 23 +
+# double cross product and combination 24 + stage update 12) - 6 + renorm 9
+RK4_FLOPS_PER_SPIN_STEP = 240.0
+BYTES_PER_SPIN_STEP_FP32 = 24.0
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            if "hbm_gbs" in d:
+                return float(d["hbm_gbs"]), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("spin_device.cuh", "step_kernels.cu"):
+        h.update(open(os.path.join(ROOT, "paper_1610_04914_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _ncu_traffic():
+    """DRAM bytes per launch of the fused step from the committed ncu summary,
+    if it was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "step_rk4_fp32_traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        d = json.load(open(path))
+        if d.get("kernel_source_sha256_16") == _kernel_source_hash():
+            return d
+    except Exception:
+        pass
+    return None
+
+
+def _params(sp, w, rank):
+    nx, ny, nz = w["n"]
+    return sp.Params(nx, ny, nz, J=w["J"], D=w["D"], H=w["H"], lam=w["lam"], T=T_BENCH, dt=w["dt"], R=w["R"],
+                     integrator=sp.RK4, precession=w["precession"], seed=w["noise_seed"], replica=rank,
+                     precision=32)
+
+
+def cpu_oracle_rate(w, budget_s=15.0, max_steps=10):
+    """Spin-steps/s of the FP64 oracle (single thread, as it stands) on the
+    full 128^3 workload: steps from the start of an interval until the time
+    budget or max_steps is reached (the pulse is step 5)."""
+    import oracle
+    oracle.build()
+    nx, ny, nz = w["n"]
+    op = oracle.Params(nx, ny, nz, J=w["J"], D=w["D"], H=w["H"], lam=w["lam"], T=T_BENCH, dt=w["dt"], R=w["R"],
+                       seed=w["noise_seed"])
+    s = spin_inputs.random_spins(nx, ny, nz, seed=w["spin_seed"])
+    t0 = time.perf_counter()
+    steps = 0
+    while steps < max_steps:
+        s, _ = oracle.run(op, s, 1, n0=steps)
+        steps += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    N = nx * ny * nz
+    return N * steps / dt, steps, dt
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return 0
+    w = spin_inputs.WORKLOADS[WORKLOAD]
+    # bounded samples: the whole run stays within about two minutes
+    budget = min(12.0, 120.0 / max(1, args.steps))
+    cpu_oracle_rate(w, budget_s=1.0, max_steps=1)   # warm-up: builds/loads the oracle
+    vals, secs, nsteps = [], 0.0, 0
+    for _ in range(args.steps):
+        v, n, dt = cpu_oracle_rate(w, budget_s=budget, max_steps=10)
+        vals.append(v)
+        secs += dt
+        nsteps += n
+    N = math.prod(w["n"])
+    value = N * nsteps / secs
+    line = {
+        "impl": "reference", "metric": "spin-steps/s (128^3 RK4 + pulse noise)", "value": value,
+        "unit": "spin-steps/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "128^3 simple-cubic ferromagnet, RK4 dt=0.2, pulse every 10 steps, T=1.0",
+                   "impl_note": "FP64 C oracle, single thread"},
+        "cpu_baseline": {"value": value, "unit": "spin-steps/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{nsteps} oracle steps of the full 128^3 lattice over {args.steps} bench steps"},
+        "e2e": {"value": value, "unit": "spin-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+
+    import paper_1610_04914_gb300 as sp
+    from paper_1610_04914_gb300 import build as b
+
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    b.build()
+    sp.load()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    w = spin_inputs.WORKLOADS[WORKLOAD]
+    p = _params(sp, w, rank)
+    N = p.N
+    R = p.R
+    s0 = spin_inputs.random_spins(p.nx, p.ny, p.nz, seed=w["spin_seed"])
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        lat = sp.Lattice(p, torch.from_numpy(s0), device=dev, stream=stream)
+        flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    # warm-up (first interval eager, later ones build and replay the graph)
+    for _ in range(max(args.warmup, 3)):
+        lat.step(R)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            lat.step(R)
+            ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - wall0
+    step_ms = [a.elapsed_time(bb) for a, bb in ev]
+    clk = clocks.stop()
+    t_dev = sum(step_ms) / 1e3
+    if ws > 1:
+        tt = torch.tensor([t_dev], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_dev = float(tt.item())
+    value = ws * N * R * args.steps / t_dev
+
+    # dominant kernel: the fused RK4 step, timed launch by launch (eager
+    # single steps, events on the launching stream, same L2 state as above)
+    kern_ms = []
+    with torch.cuda.stream(stream):
+        for k in range(max(3, args.steps)):
+            flush.zero_()
+            for q in range(R):
+                a, bb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                lat.step(1)
+                bb.record(stream)
+                if (q + 1) % R != 0:       # the sample step also launches the reduction
+                    kern_ms.append((a, bb))
+    torch.cuda.synchronize()
+    kt = [a.elapsed_time(bb) for a, bb in kern_ms]
+    t_kernel = float(np.mean(kt)) / 1e3
+    hbm_peak, peak_src = _measured_peaks()
+    achieved_gbs = BYTES_PER_SPIN_STEP_FP32 * N / t_kernel / 1e9
+    achieved_tflops = RK4_FLOPS_PER_SPIN_STEP * N / t_kernel / 1e12
+    alu_peak = SMS * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
+    traffic = _ncu_traffic()
+
+    # end to end through the public API with host buffers
+    host_in = torch.from_numpy(s0.astype(np.float32)).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    e2e_t = []
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            lat.state.copy_(host_in, non_blocking=True)
+            lat.step(R)
+            host_out.copy_(lat.state, non_blocking=True)
+            smp = lat.samples()          # synchronises the stream; reads the sample record
+            stream.synchronize()
+            e2e_t.append(time.perf_counter() - t0)
+    e2e_value = ws * N * R * args.steps / sum(e2e_t)
+    h2d = host_in.numel() * host_in.element_size()
+    d2h = host_out.numel() * host_out.element_size() + 5 * 8
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        v, nsteps, secs = cpu_oracle_rate(w, budget_s=float(os.environ.get("SPIN_CPU_BUDGET_S", "15")))
+        cpu = {"value": v, "unit": "spin-steps/s", "cores": 1, "kind": "oracle",
+               "sample": f"{nsteps} FP64 oracle steps (single thread) of the full 128^3 lattice, {secs:.1f} s"}
+
+    if rank == 0:
+        frac_hbm = achieved_gbs / hbm_peak
+        frac_alu = achieved_tflops / alu_peak
+        bound = "alu" if frac_alu >= frac_hbm else "hbm"
+        roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": frac_hbm,
+                "traffic": (traffic["dram_bytes_per_launch"] if traffic else None),
+                "peak_source": f"{peak_src} HBM copy bandwidth",
+                "kernel": "k_step_chain<float,4,32,16,PREC> (fused RK4 step, pulse in epilogue)",
+                "kernel_ms_per_launch": t_kernel * 1e3,
+                "algorithmic_bytes_per_launch": BYTES_PER_SPIN_STEP_FP32 * N}
+        alu = {"bound": "alu", "achieved": achieved_tflops, "peak": alu_peak, "unit": "TFLOP/s",
+               "frac": frac_alu, "flops_per_spin_step": RK4_FLOPS_PER_SPIN_STEP,
+               "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
+        line = {
+            "metric": "spin-steps/s (128^3 RK4 + pulse noise)", "value": value, "unit": "spin-steps/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": max(args.warmup, 3),
+            "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "128^3 simple-cubic ferromagnet, FP32 state, RK4 dt=0.2, pulse every 10 steps "
+                                   "(one bench step = one noise interval: 10 steps + pulse + FP64 sample), "
+                                   "J=1, D=0.05, H=(0,0,0.02), lambda=0.01, T=1.0",
+                       "l2": "flushed (256 MiB write) before every timed step",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+            "roofline": roof if bound == "hbm" else dict(alu, traffic=roof["traffic"], kernel=roof["kernel"],
+                                                       kernel_ms_per_launch=roof["kernel_ms_per_launch"]),
+            "roofline_hbm": roof,
+            "roofline_alu": alu,
+            "e2e": {"value": e2e_value, "unit": "spin-steps/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": args.steps * (R + 2),
+            "clocks": clk,
+            "wall_s_timed_region": wall,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    lat.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def run_profile_case(args):
+    """A small fixed case for ncu: the benchmark's physics on an L^3 FP32
+    lattice, advanced by single eager steps (step 5 of each interval carries
+    the pulse)."""
+    import torch
+
+    import paper_1610_04914_gb300 as sp
+    from paper_1610_04914_gb300 import build as b
+    b.build()
+    sp.load()
+    w = dict(spin_inputs.WORKLOADS[WORKLOAD])
+    L = args.profile_lattice
+    w["n"] = (L, L, L)
+    p = _params(sp, w, 0)
+    s0 = spin_inputs.random_spins(L, L, L, seed=w["spin_seed"])
+    lat = sp.Lattice(p, torch.from_numpy(s0), device="cuda:0")
+    for _ in range(args.profile_steps):
+        lat.step(1)
+    torch.cuda.synchronize()
+    M, E = lat.observables()
+    print(json.dumps({"profile_lattice": L, "steps": args.profile_steps, "M": M, "E": E}))
+    lat.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-lattice", type=int, default=0,
+                    help="profiling driver: L^3 FP32 RK4 lattice, --profile-steps single steps, no timing")
+    ap.add_argument("--profile-steps", type=int, default=4)
+    args = ap.parse_args()
+    ws, rank, local = _dist()
+    if args.profile_lattice:
+        return run_profile_case(args)
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+    return run_ours(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())
