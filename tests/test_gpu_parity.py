@@ -127,21 +127,21 @@ def test_fp64_trajectory_16cubed(gpu, orc):
 
 def test_fp32_trajectory_16cubed(gpu, orc):
     """FP32 state against the FP64 oracle on the 16^3 workload: 1e-5 max-abs
-    over 20 steps.  FP32 rounding (~1e-7 per component and step, at every
-    site) compounds with the system's ~2.5x-per-unit-time sensitivity; at 40
-    steps the measured gap is ~1.2e-5.  Over the full 200 steps the
-    macroscopic samples M and E, averages over 4096 spins, agree to 1e-4."""
+    over 20 steps, and the two samples (steps 10, 20) to 1e-6.  FP32 rounding
+    (~1e-7 per component and step, at every site) compounds with the system's
+    ~2.5x-per-unit-time sensitivity; at 40 steps the measured gap is ~1.2e-5
+    and by 200 steps the microscopic trajectories have decorrelated (sample
+    energies then differ by ~1e-3), so longer horizons are compared
+    statistically (equilibrium averages), not pointwise."""
     n = 16
     p = gpu.Params(n, n, n, J=1.0, D=0.0, H=(0, 0, 0.1), lam=0.1, T=1.0, dt=0.1, R=10, seed=1, precision=32)
     s0 = spin_inputs.random_spins(n, n, n, seed=0)
-    got, _ = run_gpu(gpu, p, s0, 20)
-    ref, _ = run_oracle(orc, p, s0, 20)
+    got, lat = run_gpu(gpu, p, s0, 20)
+    ref, smp = run_oracle(orc, p, s0, 20)
     assert np.max(np.abs(got - ref)) < 1e-5
-    _, lat = run_gpu(gpu, p, s0, 200)
-    _, smp = run_oracle(orc, p, s0, 200)
     rec = np.array(lat.samples())
-    assert rec.shape == smp.shape
-    assert np.max(np.abs(rec[:, 1:] - smp[:, 1:])) < 1e-4
+    assert rec.shape == smp.shape == (2, 5)
+    assert np.max(np.abs(rec[:, 1:] - smp[:, 1:])) < 1e-6
 
 
 @pytest.mark.parametrize("prec", [64, 32])
