@@ -174,6 +174,38 @@ const char* spin_last_error(const spin_lattice* h);
 int spin_noise_draw(uint64_t seed, int64_t k, int64_t replica, int64_t n_sites,
                     int32_t precision, uint64_t* words, void* gauss, void* cuda_stream);
 
+/*
+ * Observables of caller-owned spin arrays with no memory allocation at all.
+ * The paper has no counterpart: this entry point serves callers that cannot
+ * call cudaMalloc or ask their framework for memory where they need M and E
+ * (a fixed memory budget, a thread that must not enter the allocator, a
+ * plug-in that is handed only existing arrays).  It computes the same FP64
+ * values as spin_observables without a handle or workspace:
+ *   precision   32 (float arrays) or 64 (double arrays)
+ *   sx, sy, sz  device arrays of N = nx*ny*nz elements (x fastest)
+ *   h_site      nullable, device array of 3N elements (x block, y, z)
+ *   J, D, H     as in spin_params (H: host array of 3 doubles)
+ *   out5        DEVICE array of 5 doubles receiving (M_x, M_y, M_z, E, number
+ *               of non-finite spins); written asynchronously on cuda_stream.
+ * Scratch: one 5-double record per reduction block lives in a file-scope
+ * __device__ array of SPIN_NOALLOC_MAX_BLOCKS records (40 KiB); every GPU that
+ * loads the library holds it until the process exits.  All calls share it and
+ * it keeps the last call's contents; each call overwrites every record it
+ * reads, so nothing needs clearing, but calls that overlap on the GPU (two
+ * streams, or two host threads) race on it and must be serialised.  The
+ * first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any CUDA
+ * stream capture.  Lattices of more than SPIN_NOALLOC_MAX_SITES sites are
+ * rejected with SPIN_EINVAL.
+ * Errors: SPIN_EINVAL (null pointers, precision, sizes < 1 or beyond the
+ * maximum), SPIN_ECUDA.
+ */
+#define SPIN_NOALLOC_MAX_BLOCKS 1024
+#define SPIN_NOALLOC_MAX_SITES 2147483647LL
+int spin_observables_noalloc(int32_t precision, const void* sx, const void* sy, const void* sz,
+                             const void* h_site, int32_t nx, int32_t ny, int32_t nz, double J,
+                             double D, const double H[3], double* out5, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

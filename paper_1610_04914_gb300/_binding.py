@@ -21,6 +21,8 @@ SPIN_ETIMEOUT = -4
 SPIN_EUNSUPPORTED = -5
 SPIN_ENOSPACE = -6
 SPIN_SAMPLE_RING = 4096
+SPIN_NOALLOC_MAX_BLOCKS = 1024
+SPIN_NOALLOC_MAX_SITES = 2147483647
 
 RK4, RK5_BUTCHER, RK2_MIDPOINT, HEUN = 0, 1, 2, 3
 
@@ -47,7 +49,7 @@ class spin_params(ctypes.Structure):
 EXPORTS = [
     "spin_workspace_size", "spin_lattice_create", "spin_step_pulse", "spin_observables",
     "spin_samples", "spin_get_step", "spin_set_step", "spin_lattice_destroy", "spin_strerror",
-    "spin_last_error", "spin_noise_draw",
+    "spin_last_error", "spin_noise_draw", "spin_observables_noalloc",
 ]
 
 _lib = None
@@ -77,6 +79,8 @@ def load(path: str = LIB_PATH):
     L.spin_last_error.argtypes = [vp]
     L.spin_last_error.restype = ctypes.c_char_p
     L.spin_noise_draw.argtypes = [u64, i64, i64, i64, i32, vp, vp, vp]
+    d = ctypes.c_double
+    L.spin_observables_noalloc.argtypes = [i32, vp, vp, vp, vp, i32, i32, i32, d, d, P(d), vp, vp]
     for name in EXPORTS:
         if name not in ("spin_strerror", "spin_last_error"):
             getattr(L, name).restype = ctypes.c_int

@@ -148,3 +148,90 @@ template cudaError_t launch_observables<double>(const double* s[3], const double
                                                 int, double*, double*, int, long long*, long long*, int, cudaStream_t);
 
 }  // namespace spin
+
+// ---------------------------------------------------------------------------
+// Observables without any allocation by the library or the caller.
+//
+// Some callers cannot call cudaMalloc (or ask a framework to allocate) at the
+// point where they want the magnetisation and energy: code running inside a
+// strict memory budget, a host thread that must not take the allocator's
+// lock, or a plug-in that only receives pointers to existing arrays.  For
+// them this entry point keeps the reduction's scratch -- one 5-double record
+// per block of the first pass -- in a fixed file-scope device array that is
+// part of the loaded module, so nothing is allocated per call.
+// ---------------------------------------------------------------------------
+
+#include <mutex>
+
+#include "../../include/spinpulse.h"
+
+namespace spin {
+namespace {
+
+constexpr int kNoAllocMaxBlocks = SPIN_NOALLOC_MAX_BLOCKS;
+// Block records of the first reduction pass, shared by every call on a device.
+static __device__ __align__(256) double g_noalloc_partials[kNoAllocMaxBlocks * 5];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+double* g_noalloc_addr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device, looked up once
+// per device.  In host code the array's name is only a host-side stand-in,
+// so its address must come from cudaGetSymbolAddress.
+cudaError_t noalloc_scratch(double** out) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+        if (e != cudaSuccess) return e;
+        g_noalloc_addr[dev] = static_cast<double*>(p);
+    }
+    *out = g_noalloc_addr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace spin
+
+extern "C" int spin_observables_noalloc(int32_t precision, const void* sx, const void* sy, const void* sz,
+                                        const void* h_site, int32_t nx, int32_t ny, int32_t nz, double J, double D,
+                                        const double H[3], double* out5, void* cuda_stream) {
+    using namespace spin;
+    if (!sx || !sy || !sz || !out5 || !H) return SPIN_EINVAL;
+    if (precision != 32 && precision != 64) return SPIN_EINVAL;
+    if (nx < 1 || ny < 1 || nz < 1) return SPIN_EINVAL;
+    const Geom g{nx, ny, nz};
+    if (g.N() > (long long)SPIN_NOALLOC_MAX_SITES) return SPIN_EINVAL;  // beyond the stated maximum
+    const int nblocks = observables_blocks(g);
+    if (nblocks > kNoAllocMaxBlocks) return SPIN_EINVAL;
+    double* scratch = nullptr;
+    if (noalloc_scratch(&scratch) != cudaSuccess) return SPIN_ECUDA;
+    Phys<double> ph{};
+    ph.J = J;
+    ph.twoD = 2.0 * D;
+    ph.H[0] = H[0];
+    ph.H[1] = H[1];
+    ph.H[2] = H[2];
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const size_t comp = (size_t)(precision == 64 ? 8 : 4) * (size_t)g.N();
+    cudaError_t e;
+    if (precision == 32) {
+        const float* s[3] = {(const float*)sx, (const float*)sy, (const float*)sz};
+        const float* hs[3] = {nullptr, nullptr, nullptr};
+        if (h_site)
+            for (int c = 0; c < 3; ++c) hs[c] = (const float*)((const char*)h_site + c * comp);
+        e = launch_observables<float>(s, hs, g, ph, scratch, nblocks, out5, nullptr, 0, nullptr, nullptr, 1, st);
+    } else {
+        const double* s[3] = {(const double*)sx, (const double*)sy, (const double*)sz};
+        const double* hs[3] = {nullptr, nullptr, nullptr};
+        if (h_site)
+            for (int c = 0; c < 3; ++c) hs[c] = (const double*)((const char*)h_site + c * comp);
+        e = launch_observables<double>(s, hs, g, ph, scratch, nblocks, out5, nullptr, 0, nullptr, nullptr, 1, st);
+    }
+    return e == cudaSuccess ? SPIN_OK : SPIN_ECUDA;
+}

@@ -125,6 +125,19 @@ def spin_noise_draw(seed: int, k: int, replica: int, n_sites: int, precision: in
     return words, gauss
 
 
+def spin_observables_noalloc(state: torch.Tensor, J: float, D: float, H, out5: torch.Tensor,
+                             h_site: torch.Tensor | None = None, stream=None) -> None:
+    """M and E of a (3, nz, ny, nx) state into the device tensor out5 (5 doubles:
+    M_x, M_y, M_z, E, non-finite count) without any allocation; asynchronous.
+    For callers that cannot allocate device memory at the call site."""
+    _, nz, ny, nx = state.shape
+    prec = 64 if state.dtype == torch.float64 else 32
+    Hc = (ctypes.c_double * 3)(*H)
+    check(B.load().spin_observables_noalloc(prec, state[0].data_ptr(), state[1].data_ptr(), state[2].data_ptr(),
+                                            h_site.data_ptr() if h_site is not None else None, nx, ny, nz,
+                                            float(J), float(D), Hc, out5.data_ptr(), _stream_ptr(stream)))
+
+
 class Lattice:
     """Owns the device state, the optional per-site field and the workspace of
     one handle.  ``state`` is (3, nz, ny, nx) on the GPU."""
