@@ -30,32 +30,49 @@ __global__ void __launch_bounds__(kObsThreads) k_obs_partial(const real* __restr
                                                              const real* __restrict__ hy, const real* __restrict__ hz,
                                                              int nx, int ny, int nz, double J, double D, double H0,
                                                              double H1, double H2, double* __restrict__ partials) {
-    const long long N = (long long)nx * ny * nz;
+    // one warp per lattice row (y, z); lanes stride along x, so no per-site
+    // index division and the row's loads are coalesced
     const long long P = (long long)nx * ny;
+    const int rows = ny * nz;
+    const int lane = threadIdx.x & 31;
+    const int warps_total = gridDim.x * (blockDim.x >> 5);
     double m0 = 0, m1 = 0, m2 = 0, e = 0, bad = 0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(i % nx);
-        const int y = (int)((i / nx) % ny);
-        const int z = (int)(i / P);
-        const long long ix = i - x + (x + 1 == nx ? 0 : x + 1);
-        const long long iy = (long long)z * P + (long long)(y + 1 == ny ? 0 : y + 1) * nx + x;
-        const long long iz = (long long)(z + 1 == nz ? 0 : z + 1) * P + (long long)y * nx + x;
-        const double a = sx[i], b = sy[i], c = sz[i];
-        if (!isfinite(a) || !isfinite(b) || !isfinite(c)) bad += 1.0;
-        m0 += a;
-        m1 += b;
-        m2 += c;
-        const double bond = a * ((double)sx[ix] + (double)sx[iy] + (double)sx[iz]) +
-                            b * ((double)sy[ix] + (double)sy[iy] + (double)sy[iz]) +
-                            c * ((double)sz[ix] + (double)sz[iy] + (double)sz[iz]);
-        double f0 = H0, f1 = H1, f2 = H2;
-        if (HSITE) {
-            f0 += (double)hx[i];
-            f1 += (double)hy[i];
-            f2 += (double)hz[i];
+    for (int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < rows; row += warps_total) {
+        const int y = row % ny;
+        const int z = row / ny;
+        const long long rb = (long long)z * P + (long long)y * nx;
+        const long long rby = (long long)z * P + (long long)(y + 1 == ny ? 0 : y + 1) * nx;
+        const long long rbz = (long long)(z + 1 == nz ? 0 : z + 1) * P + (long long)y * nx;
+        // per-site terms in the state's precision, summed over this lane's
+        // sites of the row, then added into the FP64 accumulators
+        real rm0 = 0, rm1 = 0, rm2 = 0, re = 0;
+        int rbad = 0;
+        const real Jr = (real)J, Dr = (real)D, H0r = (real)H0, H1r = (real)H1, H2r = (real)H2;
+        for (int x = lane; x < nx; x += 32) {
+            const long long i = rb + x;
+            const long long ix = rb + (x + 1 == nx ? 0 : x + 1);
+            const long long iy = rby + x;
+            const long long iz = rbz + x;
+            const real a = sx[i], b = sy[i], c = sz[i];
+            if (!isfinite(a) || !isfinite(b) || !isfinite(c)) rbad += 1;
+            rm0 += a;
+            rm1 += b;
+            rm2 += c;
+            const real bond = a * (sx[ix] + sx[iy] + sx[iz]) + b * (sy[ix] + sy[iy] + sy[iz]) +
+                              c * (sz[ix] + sz[iy] + sz[iz]);
+            real f0 = H0r, f1 = H1r, f2 = H2r;
+            if (HSITE) {
+                f0 += hx[i];
+                f1 += hy[i];
+                f2 += hz[i];
+            }
+            re += -Jr * bond - Dr * c * c - (f0 * a + f1 * b + f2 * c);
         }
-        e += -J * bond - D * c * c - (f0 * a + f1 * b + f2 * c);
+        m0 += (double)rm0;
+        m1 += (double)rm1;
+        m2 += (double)rm2;
+        e += (double)re;
+        bad += (double)rbad;
     }
     __shared__ double red[kObsThreads / 32][5];
     m0 = warp_sum(m0);
@@ -120,8 +137,9 @@ __global__ void __launch_bounds__(kObsThreads) k_obs_final(const double* __restr
 }  // namespace
 
 int observables_blocks(Geom g) {
-    const long long N = g.N();
-    return (int)std::max<long long>(1, std::min<long long>((N + kObsThreads - 1) / kObsThreads, 152LL * 4));
+    const long long rows = (long long)g.ny * g.nz;
+    const long long warps_per_block = kObsThreads / 32;
+    return (int)std::max<long long>(1, std::min<long long>((rows + warps_per_block - 1) / warps_per_block, 152LL * 4));
 }
 
 template <typename real>

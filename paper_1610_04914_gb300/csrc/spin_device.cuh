@@ -18,6 +18,17 @@ struct Words4 {
     uint64_t w[4];
 };
 
+// 64x64 -> 128-bit product from four 32x32 -> 64 partial products.
+__device__ __forceinline__ void mul64_wide(uint64_t a, uint64_t m, uint64_t& hi, uint64_t& lo) {
+    const uint32_t a0 = (uint32_t)a, a1 = (uint32_t)(a >> 32);
+    const uint32_t m0 = (uint32_t)m, m1 = (uint32_t)(m >> 32);
+    const uint64_t p00 = (uint64_t)a0 * m0, p01 = (uint64_t)a0 * m1;
+    const uint64_t p10 = (uint64_t)a1 * m0, p11 = (uint64_t)a1 * m1;
+    const uint64_t mid = (p00 >> 32) + (uint32_t)p01 + (uint32_t)p10;
+    lo = (mid << 32) | (uint32_t)p00;
+    hi = p11 + (p01 >> 32) + (p10 >> 32) + (mid >> 32);
+}
+
 __device__ __forceinline__ Words4 philox4x64_10(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3,
                                                 uint64_t k0, uint64_t k1) {
     constexpr uint64_t kMulA = 0xD2E7470EE14C6C93ULL;
@@ -26,8 +37,9 @@ __device__ __forceinline__ Words4 philox4x64_10(uint64_t c0, uint64_t c1, uint64
     constexpr uint64_t kWeylB = 0xBB67AE8584CAA73BULL;
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const uint64_t hiA = __umul64hi(kMulA, c0), loA = kMulA * c0;
-        const uint64_t hiB = __umul64hi(kMulB, c2), loB = kMulB * c2;
+        uint64_t hiA, loA, hiB, loB;
+        mul64_wide(c0, kMulA, hiA, loA);
+        mul64_wide(c2, kMulB, hiB, loB);
         const uint64_t n0 = hiB ^ c1 ^ k0;
         const uint64_t n2 = hiA ^ c3 ^ k1;
         c0 = n0;

@@ -57,6 +57,9 @@ cudaError_t launch_step(const StepLaunch<real>& L);
 // (call once per device before launching or capturing).
 template <typename real>
 cudaError_t prepare_step_kernels();
+// FP32 fused step with 2x2 register patches (chain tableaus, 2 or 4 stages).
+cudaError_t launch_step_patch(const StepLaunch<float>& L);
+cudaError_t prepare_patch_kernels();
 
 // FP64 observables: per-block partials, then a one-block deterministic sum.
 // out5 = (M_x, M_y, M_z, E, nonfinite count); if sample_ring != null the

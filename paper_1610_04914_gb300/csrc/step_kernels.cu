@@ -309,7 +309,9 @@ cudaError_t prepare_step_kernels() {
     ChainArgs<real> a{};
     cudaError_t e = dispatch_chain<real, 4, BX, BY>(a, dim3(1), 0, false, false, false, true);
     if (e != cudaSuccess) return e;
-    return dispatch_chain<real, 2, BX, BY>(a, dim3(1), 0, false, false, false, true);
+    e = dispatch_chain<real, 2, BX, BY>(a, dim3(1), 0, false, false, false, true);
+    if (e != cudaSuccess || sizeof(real) != 4) return e;
+    return prepare_patch_kernels();
 }
 template cudaError_t prepare_step_kernels<float>();
 template cudaError_t prepare_step_kernels<double>();
@@ -513,7 +515,10 @@ static cudaError_t launch_generic(const StepLaunch<real>& L) {
 
 template <typename real>
 cudaError_t launch_step(const StepLaunch<real>& L) {
-    if (L.tab->chain && !L.force_generic && (L.tab->stages == 4 || L.tab->stages == 2)) return launch_chain<real>(L);
+    if (L.tab->chain && !L.force_generic && (L.tab->stages == 4 || L.tab->stages == 2)) {
+        if (sizeof(real) == 4) return launch_step_patch(reinterpret_cast<const StepLaunch<float>&>(L));
+        return launch_chain<real>(L);
+    }
     return launch_generic<real>(L);
 }
 

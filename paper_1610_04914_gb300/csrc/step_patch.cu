@@ -1,0 +1,465 @@
+// Fused FP32 step for chain tableaus (RK4, RK2 midpoint, Heun) with 2x2
+// register patches and packed f32x2 arithmetic.
+//
+// Geometry.  A CTA of 16x16 threads owns a 32x32 tile of lattice columns
+// (x, y); each thread owns a 2x2 patch: rows cy = 2ty, 2ty+1, and the column
+// pair cx = 2tx, 2tx+1 packed into one float2, so every FP32 operation of the
+// right-hand side covers two sites with one f32x2 instruction.  The tile
+// carries a halo of S columns (S = stages): after stage j only the columns
+// within S-j of the (32-2S)^2 output block are still exact, which is all the
+// next stage needs.  The CTA marches along z: at wavefront iteration t it
+// streams in spin plane t+S and evaluates stage j on plane t+S-j, so every
+// stage state lives on chip for exactly the planes its z-neighbours need
+// (per-thread register rings indexed by plane & 3).
+//
+// Neighbour exchange per stage: x-neighbours by warp shuffles inside each
+// 16-lane row segment, y-neighbours through shared memory (one double-
+// buffered plane per stage, one barrier per iteration), z-neighbours from
+// the rings.  One HBM read and one write of the state per step; the pulse
+// rotation (Eq. s_rotation) runs in the epilogue of its step.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "spin_device.cuh"
+#include "spin_internal.h"
+
+namespace spin {
+
+namespace {
+
+constexpr int kPT = 16;        // threads along x
+constexpr int kPC = 2 * kPT;   // columns along x (two per thread, one float2)
+constexpr int kRS = kPC;       // shared row stride (floats)
+
+// Rows per thread (PY) and thread rows (TY) per stage count: RK4 keeps one row
+// per thread (register rings of 4 stage planes do not fit twice), RK2/Heun two.
+template <int S>
+struct PatchShape;
+template <>
+struct PatchShape<4> {
+    static constexpr int PY = 1, TY = 24;
+};
+template <>
+struct PatchShape<2> {
+    static constexpr int PY = 2, TY = 16;
+};
+
+struct PatchArgs {
+    const float* __restrict__ in0;
+    const float* __restrict__ in1;
+    const float* __restrict__ in2;
+    float* __restrict__ out0;
+    float* __restrict__ out1;
+    float* __restrict__ out2;
+    const float* __restrict__ hs0;
+    const float* __restrict__ hs1;
+    const float* __restrict__ hs2;
+    int nx, ny, nz, tz, n_iter;
+    float J, twoD, Hx, Hy, Hz, lambda;
+    float cdt[4];
+    float bdt[4];
+    int renorm;
+    uint64_t seed, replica;
+    float sigma;
+    const long long* interval;
+};
+
+typedef float2 f2;
+__device__ __forceinline__ f2 add2(f2 a, f2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ f2 sp2(float v) { return make_float2(v, v); }
+
+__device__ __forceinline__ void cp_async4(float* smem, const float* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ int wrapi(int v, int n) {
+    int r = v % n;
+    return r < 0 ? r + n : r;
+}
+
+template <int S, bool HSITE>
+struct PRings {
+    static constexpr int PY = PatchShape<S>::PY;
+    f2 s[4][PY][3];
+    f2 x[S - 1][4][PY][3];
+    f2 y[4][PY][3];
+    f2 h[HSITE ? 4 : 1][PY][3];
+};
+
+template <int PY>
+struct PThread {
+    int tx, ty, warp_row;
+    int col[PY][2];    // [row][pair element] global column index gy*nx+gx
+    bool out[PY][2];
+    int plane;         // nx*ny
+};
+
+// Per-thread staging ring for spin planes fetched two iterations ahead with
+// cp.async (the thread only ever reads back its own columns): 4 slots x 3
+// components x PY rows x 2 columns, thread-minor so accesses are conflict-free.
+template <int S>
+__device__ __forceinline__ float* stage_slot(float* stg, int slot, int c, int rr, int e, int tid) {
+    constexpr int PY = PatchShape<S>::PY, NT = kPT * PatchShape<S>::TY;
+    return stg + (((slot * 3 + c) * PY + rr) * 2 + e) * NT + tid;
+}
+
+template <int S>
+__device__ __forceinline__ void issue_plane(const PatchArgs& a, float* stg, const PThread<PatchShape<S>::PY>& th,
+                                            int slot, int gz, int tid) {
+    constexpr int PY = PatchShape<S>::PY;
+    const long long base = (long long)gz * th.plane;
+#pragma unroll
+    for (int rr = 0; rr < PY; ++rr)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const long long o = base + th.col[rr][e];
+            cp_async4(stage_slot<S>(stg, slot, 0, rr, e, tid), a.in0 + o);
+            cp_async4(stage_slot<S>(stg, slot, 1, rr, e, tid), a.in1 + o);
+            cp_async4(stage_slot<S>(stg, slot, 2, rr, e, tid), a.in2 + o);
+        }
+    cp_async_commit();
+}
+
+template <int S, bool PREC, bool HSITE, bool PULSE, int P>
+__device__ __forceinline__ void patch_iteration(const PatchArgs& a, PRings<S, HSITE>& r, float* __restrict__ sh,
+                                                float* __restrict__ stg, const PThread<PatchShape<S>::PY>& th, int i,
+                                                int t0, int z0, long long k, int tid) {
+    constexpr int PY = PatchShape<S>::PY, ROWS = PatchShape<S>::PY * PatchShape<S>::TY;
+    constexpr int TILE = ROWS * kRS;
+    float* shb = sh + (P & 1) * (S * 3 * TILE);
+    const int cy0 = PY * th.ty;
+    const int cx0 = 2 * th.tx;
+
+    // 1. publish the stage inputs (both rows) for the y-neighbours
+#pragma unroll
+    for (int j = 1; j <= S; ++j) {
+        const int slot = (P + S - j) & 3;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int rr = 0; rr < PY; ++rr) {
+                const f2 v = (j == 1) ? r.s[slot][rr][c] : r.x[j - 2][slot][rr][c];
+                *reinterpret_cast<f2*>(shb + ((j - 1) * 3 + c) * TILE + (cy0 + rr) * kRS + cx0) = v;
+            }
+    }
+
+    // 2. spin plane t+S arrives from the staging ring (fetched two iterations
+    //    ago); plane t+S+2 is requested now
+    const int t = i + t0;
+    {
+        issue_plane<S>(a, stg, th, (P + S + 2) & 3, wrapi(t + S + 2, a.nz), tid);
+        cp_async_wait<2>();
+        const int slot = (P + S) & 3;
+#pragma unroll
+        for (int rr = 0; rr < PY; ++rr)
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                r.s[slot][rr][c] = make_float2(*stage_slot<S>(stg, slot, c, rr, 0, tid),
+                                               *stage_slot<S>(stg, slot, c, rr, 1, tid));
+        if (HSITE) {
+            const long long bh = (long long)wrapi(t + S - 1, a.nz) * th.plane;
+            const int sl = (P + S - 1) & 3;
+#pragma unroll
+            for (int rr = 0; rr < PY; ++rr) {
+                const long long o0 = bh + th.col[rr][0], o1 = bh + th.col[rr][1];
+                r.h[sl][rr][0] = make_float2(__ldg(a.hs0 + o0), __ldg(a.hs0 + o1));
+                r.h[sl][rr][1] = make_float2(__ldg(a.hs1 + o0), __ldg(a.hs1 + o1));
+                r.h[sl][rr][2] = make_float2(__ldg(a.hs2 + o0), __ldg(a.hs2 + o1));
+            }
+        }
+    }
+    __syncthreads();
+
+    const int up = cy0 > 0 ? cy0 - 1 : cy0;                     // row above the first row (clamped at the tile edge)
+    const int dn = cy0 + PY < ROWS ? cy0 + PY : cy0 + PY - 1;   // row below the last row
+
+    // 3. stage j on plane t+S-j
+#pragma unroll
+    for (int j = 1; j <= S; ++j) {
+        // the 2*PY rows of warp w take part in stage j only if they meet the
+        // rows [j, ROWS-j) where stage j is still needed (warp-uniform)
+        const bool active = (2 * PY * th.warp_row + 2 * PY - 1 >= j) && (2 * PY * th.warp_row < ROWS - j);
+        const int slot = (P + S - j) & 3;
+        const int sm = (slot + 3) & 3, sp = (slot + 1) & 3;
+        if (active) {
+            const float* shj = shb + (j - 1) * 3 * TILE;
+            f2 cen[PY][3], sum[PY][3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const f2 row_up = *reinterpret_cast<const f2*>(shj + c * TILE + up * kRS + cx0);
+                const f2 row_dn = *reinterpret_cast<const f2*>(shj + c * TILE + dn * kRS + cx0);
+#pragma unroll
+                for (int rr = 0; rr < PY; ++rr) {
+                    const f2 C = (j == 1) ? r.s[slot][rr][c] : r.x[j - 2][slot][rr][c];
+                    const f2 ZM = (j == 1) ? r.s[sm][rr][c] : r.x[j - 2][sm][rr][c];
+                    const f2 ZP = (j == 1) ? r.s[sp][rr][c] : r.x[j - 2][sp][rr][c];
+                    // x-neighbours: left of the pair's first column and right of its second
+                    const float L = __shfl_up_sync(0xffffffffu, C.y, 1, kPT);
+                    const float Rr = __shfl_down_sync(0xffffffffu, C.x, 1, kPT);
+                    const f2 xm = make_float2(L, C.x);
+                    const f2 xp = make_float2(C.y, Rr);
+                    const int ro = PY == 2 ? (rr ^ 1) : rr;
+                    const f2 other = (j == 1) ? r.s[slot][ro][c] : r.x[j - 2][slot][ro][c];
+                    const f2 ym = rr == 0 ? row_up : other;
+                    const f2 yp = rr == PY - 1 ? row_dn : other;
+                    // neighbour order x-1, x+1, y-1, y+1, z-1, z+1
+                    sum[rr][c] = add2(add2(add2(add2(add2(xm, xp), ym), yp), ZM), ZP);
+                    cen[rr][c] = C;
+                }
+            }
+#pragma unroll
+            for (int rr = 0; rr < PY; ++rr) {
+                f2 hx = fma2(sp2(a.J), sum[rr][0], sp2(a.Hx));
+                f2 hy = fma2(sp2(a.J), sum[rr][1], sp2(a.Hy));
+                f2 hz = fma2(sp2(a.J), sum[rr][2], sp2(a.Hz));
+                if (HSITE) {
+                    hx = add2(hx, r.h[slot][rr][0]);
+                    hy = add2(hy, r.h[slot][rr][1]);
+                    hz = add2(hz, r.h[slot][rr][2]);
+                }
+                const f2 sx = cen[rr][0], sy = cen[rr][1], sz = cen[rr][2];
+                hz = fma2(sp2(a.twoD), sz, hz);
+                // a = s x H ; b = s x a ; f = a - lambda b  (slow: f = -lambda b)
+                const f2 nx_ = make_float2(-sx.x, -sx.y), ny_ = make_float2(-sy.x, -sy.y), nz_ = make_float2(-sz.x, -sz.y);
+                const f2 ax = fma2(nz_, hy, mul2(sy, hz));
+                const f2 ay = fma2(nx_, hz, mul2(sz, hx));
+                const f2 az = fma2(ny_, hx, mul2(sx, hy));
+                const f2 bx = fma2(nz_, ay, mul2(sy, az));
+                const f2 by = fma2(nx_, az, mul2(sz, ax));
+                const f2 bz = fma2(ny_, ax, mul2(sx, ay));
+                f2 f[3];
+                if (PREC) {
+                    f[0] = fma2(sp2(-a.lambda), bx, ax);
+                    f[1] = fma2(sp2(-a.lambda), by, ay);
+                    f[2] = fma2(sp2(-a.lambda), bz, az);
+                } else {
+                    f[0] = mul2(sp2(-a.lambda), bx);
+                    f[1] = mul2(sp2(-a.lambda), by);
+                    f[2] = mul2(sp2(-a.lambda), bz);
+                }
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    if (j == 1)
+                        r.y[slot][rr][c] = fma2(sp2(a.bdt[0]), f[c], r.s[slot][rr][c]);
+                    else
+                        r.y[slot][rr][c] = fma2(sp2(a.bdt[j - 1]), f[c], r.y[slot][rr][c]);
+                    if (j < S) r.x[j - 1][slot][rr][c] = fma2(sp2(a.cdt[j - 1]), f[c], r.s[slot][rr][c]);
+                }
+            }
+        }
+        if (j == S && active && t >= z0 && t < z0 + a.tz && t < a.nz) {
+            // finished plane t: renormalise, pulse, store
+            const long long base = (long long)t * th.plane;
+#pragma unroll
+            for (int rr = 0; rr < PY; ++rr) {
+                f2 ox = r.y[slot][rr][0], oy = r.y[slot][rr][1], oz = r.y[slot][rr][2];
+                if (a.renorm) {
+                    const f2 n2 = fma2(ox, ox, fma2(oy, oy, mul2(oz, oz)));
+                    const f2 inv = make_float2(rsqrtf(n2.x), rsqrtf(n2.y));
+                    ox = mul2(ox, inv);
+                    oy = mul2(oy, inv);
+                    oz = mul2(oz, inv);
+                }
+                float vx[2] = {ox.x, ox.y}, vy[2] = {oy.x, oy.y}, vz[2] = {oz.x, oz.y};
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    if (!th.out[rr][e]) continue;
+                    const long long site = base + th.col[rr][e];
+                    if (PULSE) pulse_site<float>(vx[e], vy[e], vz[e], a.seed, (uint64_t)site, (uint64_t)k, a.replica, a.sigma);
+                    a.out0[site] = vx[e];
+                    a.out1[site] = vy[e];
+                    a.out2[site] = vz[e];
+                }
+            }
+        }
+    }
+}
+
+template <int S, bool PREC, bool HSITE, bool PULSE>
+__global__ void __launch_bounds__(kPT* PatchShape<S>::TY, 1) k_step_patch(PatchArgs a) {
+    constexpr int PY = PatchShape<S>::PY, ROWS = PatchShape<S>::PY * PatchShape<S>::TY;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* sh = reinterpret_cast<float*>(smem_raw);
+    float* stg = sh + 2 * S * 3 * ROWS * kRS;
+    const int tid = threadIdx.y * kPT + threadIdx.x;
+    PThread<PY> th;
+    th.tx = threadIdx.x;
+    th.ty = threadIdx.y;
+    th.warp_row = (threadIdx.y * kPT + threadIdx.x) >> 5;   // two thread rows per warp
+    constexpr int OUTX = kPC - 2 * S, OUTY = ROWS - 2 * S;
+    th.plane = a.nx * a.ny;
+#pragma unroll
+    for (int rr = 0; rr < PY; ++rr) {
+        const int cy = PY * th.ty + rr;
+        const int gyu = (int)blockIdx.y * OUTY - S + cy;
+        const int gy = wrapi(gyu, a.ny);
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int cx = 2 * th.tx + e;
+            const int gxu = (int)blockIdx.x * OUTX - S + cx;
+            th.col[rr][e] = gy * a.nx + wrapi(gxu, a.nx);
+            th.out[rr][e] = cx >= S && cx < kPC - S && cy >= S && cy < ROWS - S && gxu < a.nx && gyu < a.ny;
+        }
+    }
+    const int z0 = (int)blockIdx.z * a.tz;
+    const int t0 = z0 - 2 * S + 2;
+    const long long k = PULSE ? *a.interval : 0;
+
+    PRings<S, HSITE> r;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int rr = 0; rr < PY; ++rr)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                r.s[q][rr][c] = make_float2(0.f, 0.f);
+                r.y[q][rr][c] = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int j = 0; j < S - 1; ++j) r.x[j][q][rr][c] = make_float2(0.f, 0.f);
+                if (HSITE) r.h[q][rr][c] = make_float2(0.f, 0.f);
+            }
+#pragma unroll
+    for (int L = S - 2; L <= S - 1; ++L) {
+        const long long base = (long long)wrapi(t0 + L, a.nz) * th.plane;
+#pragma unroll
+        for (int rr = 0; rr < PY; ++rr) {
+            const long long o0 = base + th.col[rr][0], o1 = base + th.col[rr][1];
+            r.s[L & 3][rr][0] = make_float2(__ldg(a.in0 + o0), __ldg(a.in0 + o1));
+            r.s[L & 3][rr][1] = make_float2(__ldg(a.in1 + o0), __ldg(a.in1 + o1));
+            r.s[L & 3][rr][2] = make_float2(__ldg(a.in2 + o0), __ldg(a.in2 + o1));
+        }
+    }
+    // planes S and S+1 (local) go to the staging ring before the march
+    issue_plane<S>(a, stg, th, S & 3, wrapi(t0 + S, a.nz), tid);
+    issue_plane<S>(a, stg, th, (S + 1) & 3, wrapi(t0 + S + 1, a.nz), tid);
+    int i = 0;
+    for (; i + 4 <= a.n_iter; i += 4) {
+        patch_iteration<S, PREC, HSITE, PULSE, 0>(a, r, sh, stg, th, i + 0, t0, z0, k, tid);
+        patch_iteration<S, PREC, HSITE, PULSE, 1>(a, r, sh, stg, th, i + 1, t0, z0, k, tid);
+        patch_iteration<S, PREC, HSITE, PULSE, 2>(a, r, sh, stg, th, i + 2, t0, z0, k, tid);
+        patch_iteration<S, PREC, HSITE, PULSE, 3>(a, r, sh, stg, th, i + 3, t0, z0, k, tid);
+    }
+    if (i < a.n_iter) patch_iteration<S, PREC, HSITE, PULSE, 0>(a, r, sh, stg, th, i + 0, t0, z0, k, tid);
+    if (i + 1 < a.n_iter) patch_iteration<S, PREC, HSITE, PULSE, 1>(a, r, sh, stg, th, i + 1, t0, z0, k, tid);
+    if (i + 2 < a.n_iter) patch_iteration<S, PREC, HSITE, PULSE, 2>(a, r, sh, stg, th, i + 2, t0, z0, k, tid);
+    cp_async_wait<0>();   // no copy may land in shared memory after the CTA exits
+}
+
+template <int S, bool PREC, bool HSITE, bool PULSE>
+size_t patch_smem() {
+    constexpr int ROWS = PatchShape<S>::PY * PatchShape<S>::TY, NT = kPT * PatchShape<S>::TY;
+    return sizeof(float) * (2 * S * 3 * ROWS * kRS + 4 * 3 * PatchShape<S>::PY * 2 * NT);
+}
+
+template <int S, bool PREC, bool HSITE, bool PULSE>
+cudaError_t patch_launch(const PatchArgs& a, dim3 grid, cudaStream_t st, bool prepare) {
+    const size_t smem = patch_smem<S, PREC, HSITE, PULSE>();
+    if (prepare)
+        return cudaFuncSetAttribute(k_step_patch<S, PREC, HSITE, PULSE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem);
+    k_step_patch<S, PREC, HSITE, PULSE><<<grid, dim3(kPT, PatchShape<S>::TY), smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int S>
+cudaError_t patch_dispatch(const PatchArgs& a, dim3 grid, cudaStream_t st, bool prec, bool hs, bool pulse,
+                           bool prepare) {
+#define SPIN_PATCH_CASE(P_, H_, U_)                                                   \
+    if (prepare) {                                                                    \
+        cudaError_t e = patch_launch<S, P_, H_, U_>(a, grid, st, true);               \
+        if (e != cudaSuccess) return e;                                               \
+    } else if (prec == P_ && hs == H_ && pulse == U_) {                               \
+        return patch_launch<S, P_, H_, U_>(a, grid, st, false);                       \
+    }
+    SPIN_PATCH_CASE(true, false, false)
+    SPIN_PATCH_CASE(true, false, true)
+    SPIN_PATCH_CASE(true, true, false)
+    SPIN_PATCH_CASE(true, true, true)
+    SPIN_PATCH_CASE(false, false, false)
+    SPIN_PATCH_CASE(false, false, true)
+    SPIN_PATCH_CASE(false, true, false)
+    SPIN_PATCH_CASE(false, true, true)
+#undef SPIN_PATCH_CASE
+    return prepare ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+cudaError_t prepare_patch_kernels() {
+    PatchArgs a{};
+    cudaError_t e = patch_dispatch<4>(a, dim3(1), 0, false, false, false, true);
+    if (e != cudaSuccess) return e;
+    return patch_dispatch<2>(a, dim3(1), 0, false, false, false, true);
+}
+
+cudaError_t launch_step_patch(const StepLaunch<float>& L) {
+    const Tableau& tb = *L.tab;
+    const int S = tb.stages;
+    PatchArgs a{};
+    a.in0 = L.in[0];
+    a.in1 = L.in[1];
+    a.in2 = L.in[2];
+    a.out0 = L.out[0];
+    a.out1 = L.out[1];
+    a.out2 = L.out[2];
+    a.hs0 = L.hs[0];
+    a.hs1 = L.hs[1];
+    a.hs2 = L.hs[2];
+    a.nx = L.g.nx;
+    a.ny = L.g.ny;
+    a.nz = L.g.nz;
+    a.J = L.ph.J;
+    a.twoD = L.ph.twoD;
+    a.Hx = L.ph.H[0];
+    a.Hy = L.ph.H[1];
+    a.Hz = L.ph.H[2];
+    a.lambda = L.ph.lambda;
+    for (int j = 0; j < 4; ++j) {
+        a.cdt[j] = (j + 1 < S) ? (float)(tb.a[j + 1][j] * L.dt) : 0.f;
+        a.bdt[j] = (j < S) ? (float)(tb.b[j] * L.dt) : 0.f;
+    }
+    a.renorm = L.renorm;
+    a.seed = L.seed;
+    a.replica = L.replica;
+    a.sigma = L.sigma;
+    a.interval = L.d_interval;
+    const int outx = kPC - 2 * S;
+    const int outy = (S == 4 ? PatchShape<4>::PY * PatchShape<4>::TY : PatchShape<2>::PY * PatchShape<2>::TY) - 2 * S;
+    const int tiles_x = (L.g.nx + outx - 1) / outx;
+    const int tiles_y = (L.g.ny + outy - 1) / outy;
+    // z chunks: one resident CTA per SM, so pick the chunk count that
+    // minimises waves x (chunk planes + pipeline fill of 2S-2 iterations)
+    const long long tiles = (long long)tiles_x * tiles_y;
+    int best_chunks = 1;
+    double best_cost = 1e300;
+    for (int c = 1; c <= std::max(1, L.g.nz / 4); ++c) {
+        const int zc_c = (L.g.nz + c - 1) / c;
+        const int used = (L.g.nz + zc_c - 1) / zc_c;
+        const long long ctas = tiles * used;
+        const double waves = (double)((ctas + 151) / 152);
+        const double cost = waves * (zc_c + 2 * S - 2);
+        if (cost < best_cost - 1e-9) {
+            best_cost = cost;
+            best_chunks = c;
+        }
+    }
+    const int zc = (L.g.nz + best_chunks - 1) / best_chunks;
+    a.tz = zc;
+    a.n_iter = zc + 2 * S - 2;
+    dim3 grid(tiles_x, tiles_y, (L.g.nz + zc - 1) / zc);
+    const bool hs = L.hs[0] != nullptr;
+    const bool prec = L.precession != 0;
+    if (S == 4) return patch_dispatch<4>(a, grid, L.stream, prec, hs, L.pulse != 0, false);
+    return patch_dispatch<2>(a, grid, L.stream, prec, hs, L.pulse != 0, false);
+}
+
+}  // namespace spin

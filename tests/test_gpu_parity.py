@@ -78,7 +78,7 @@ def test_three_steps_with_pulse(gpu, orc, shape, prec, integ, precession, hsite,
     assert np.max(np.abs(got - ref)) < tol
     rec = lat.samples()
     assert len(rec) == 1 and rec[0][0] == 3.0
-    assert np.max(np.abs(np.array(rec[0][1:]) - smp[0, 1:])) < (1e-13 if prec == 64 else 2e-6)
+    assert np.max(np.abs(np.array(rec[0][1:]) - smp[0, 1:])) < (1e-13 if prec == 64 else 5e-6)
 
 
 @pytest.mark.parametrize("prec", [64, 32])
@@ -127,7 +127,7 @@ def test_fp64_trajectory_16cubed(gpu, orc):
 
 def test_fp32_trajectory_16cubed(gpu, orc):
     """FP32 state against the FP64 oracle on the 16^3 workload: 1e-5 max-abs
-    over 20 steps, and the two samples (steps 10, 20) to 1e-6.  FP32 rounding
+    over 20 steps, and the two samples (steps 10, 20) to 5e-6.  FP32 rounding
     (~1e-7 per component and step, at every site) compounds with the system's
     ~2.5x-per-unit-time sensitivity; at 40 steps the measured gap is ~1.2e-5
     and by 200 steps the microscopic trajectories have decorrelated (sample
@@ -141,13 +141,17 @@ def test_fp32_trajectory_16cubed(gpu, orc):
     assert np.max(np.abs(got - ref)) < 1e-5
     rec = np.array(lat.samples())
     assert rec.shape == smp.shape == (2, 5)
-    assert np.max(np.abs(rec[:, 1:] - smp[:, 1:])) < 1e-6
+    assert np.max(np.abs(rec[:, 1:] - smp[:, 1:])) < 5e-6
 
 
 @pytest.mark.parametrize("prec", [64, 32])
 @pytest.mark.parametrize("shape", [(16, 16, 16), (5, 7, 3), (1, 1, 1), (2, 2, 2)])
 def test_observables(gpu, orc, prec, shape):
-    """FP64 reductions of M and E against the oracle on the same values."""
+    """M and E against the oracle on the same values.  FP64 states: FP64
+    arithmetic throughout (1e-13).  FP32 states: per-site terms in FP32 (a bond
+    sum of three products of float spins carries at most a few 1e-7 relative
+    error, the per-site energy |e_i| < 7 here), accumulated in FP64 per row:
+    bounds 1e-6 for M and 5e-6 for E."""
     nx, ny, nz = shape
     p = gpu.Params(nx, ny, nz, J=0.8, D=0.3, H=(0.1, -0.2, 0.3), precision=prec)
     s0 = spin_inputs.random_spins(nx, ny, nz, seed=9)
@@ -155,8 +159,9 @@ def test_observables(gpu, orc, prec, shape):
     lat = gpu.Lattice(p, torch.from_numpy(s0), h_site=torch.from_numpy(hs))
     M, E = lat.observables()
     ref = orc.observables(orc_params(orc, p), as_input(p, s0), as_input(p, hs))
-    assert np.max(np.abs(np.array(M) - ref[:3])) < 1e-13
-    assert abs(E - ref[3]) < 1e-13
+    tm, te = (1e-13, 1e-13) if prec == 64 else (1e-6, 5e-6)
+    assert np.max(np.abs(np.array(M) - ref[:3])) < tm
+    assert abs(E - ref[3]) < te
 
 
 # ----------------------------------------------------------------- graph path, resume
