@@ -110,6 +110,10 @@ def lib():
         L.orc_run.restype = i64
         L.orc_metropolis.argtypes = [P(_Params), P(d), P(d), u64, d, i64, i64, P(d)]
         L.orc_metropolis.restype = i64
+        L.orc_rhs_vjp.argtypes = [P(_Params), P(d), P(d), P(d), P(d), P(d), P(d), P(d), P(d)]
+        L.orc_step_vjp.argtypes = [P(_Params), P(d), P(d), ctypes.c_int, i64, P(d), P(d), P(d), P(d), P(d)]
+        L.orc_adjoint.argtypes = [P(_Params), P(d), P(d), i64, i64, ctypes.c_int, P(d), d, P(d), P(d), P(d),
+                                  P(d), P(d)]
         _lib = L
     return _lib
 
@@ -241,3 +245,48 @@ def metropolis(p: Params, s, nsweeps: int, mc_seed: int, R_trial=None, sweep0: i
     acc = lib().orc_metropolis(ctypes.byref(p.c()), _dp(a), _dp(hs), mc_seed & 0xFFFFFFFFFFFFFFFF,
                                float(R_trial), sweep0, nsweeps, _dp(ser))
     return a, ser, int(acc)
+
+
+# ---------------------------------------------------------------- adjoint
+def rhs_vjp(p: Params, x, v, h_site=None):
+    """(J_f(x)^T v, dJ, dD, dH[3], dh[3N]): transpose of the right-hand side's
+    Jacobian applied to v, and <v, df/dtheta> for theta = J, D, H, h_i."""
+    xa = _state(p, x)
+    va = _state(p, v)
+    hs = _field(p, h_site)
+    out = np.empty_like(xa)
+    gJ, gD = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    gH = np.zeros(3)
+    gh = np.zeros_like(xa)
+    lib().orc_rhs_vjp(ctypes.byref(p.c()), _dp(xa), _dp(hs), _dp(va), _dp(out), ctypes.byref(gJ),
+                      ctypes.byref(gD), _dp(gH), _dp(gh))
+    return out, gJ.value, gD.value, gH, gh
+
+
+def step_vjp(p: Params, s, lam, pulse: bool = False, k: int = 0, h_site=None):
+    """dL/ds_before from dL/ds_after = lam for one step taken from s, with the
+    parameter gradients of that step: (lam_before, dJ, dD, dH, dh)."""
+    sa = _state(p, s)
+    la = _state(p, lam)
+    hs = _field(p, h_site)
+    gJ, gD = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    gH = np.zeros(3)
+    gh = np.zeros_like(sa)
+    lib().orc_step_vjp(ctypes.byref(p.c()), _dp(sa), _dp(hs), int(pulse), k, _dp(la), ctypes.byref(gJ),
+                       ctypes.byref(gD), _dp(gH), _dp(gh))
+    return la, gJ.value, gD.value, gH, gh
+
+
+def adjoint(p: Params, s0, nsteps: int, dLdM, dLdE: float, n0: int = 0, h_site=None, noise: bool = True):
+    """Gradients of L = dLdE E(s_n) + dLdM.M(s_n) (E, M per spin) after nsteps
+    steps: dict with J, D, H (3,), h (3N field gradient) and s0 (dL/ds_0)."""
+    sa = _state(p, s0)
+    hs = _field(p, h_site)
+    gJ, gD = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    gH = np.zeros(3)
+    gh = np.zeros_like(sa)
+    gs = np.zeros_like(sa)
+    dm = np.asarray(dLdM, dtype=np.float64)
+    lib().orc_adjoint(ctypes.byref(p.c()), _dp(sa), _dp(hs), n0, nsteps, int(noise), _dp(dm), float(dLdE),
+                      ctypes.byref(gJ), ctypes.byref(gD), _dp(gH), _dp(gh), _dp(gs))
+    return {"J": gJ.value, "D": gD.value, "H": gH, "h": gh, "s0": gs}

@@ -463,3 +463,233 @@ int64_t orc_metropolis(const orc_params *p, double *s, const double *hsite,
     }
     return accepted;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Discrete adjoint (pathwise, noise fixed) of the whole step: RK stages,    */
+/* renormalisation and the pulse rotation, for losses of the final state     */
+/* L = dLdE E(s_n) + dLdM . M(s_n).  Gradients w.r.t. J, D, H, h_i and s_0.  */
+/* Pinned by central finite differences of L and by dot-product tests of    */
+/* each primitive's transpose.                                               */
+/* ------------------------------------------------------------------------ */
+
+/* Butcher arrays of the integrators above: K_j = h f(x_j),
+   x_j = x + sum_{l<j} a[j][l] K_l, x' = x + sum_j b[j] K_j. */
+static int tableau(int integrator, double a[6][6], double b[6])
+{
+    memset(a, 0, sizeof(double) * 36);
+    memset(b, 0, sizeof(double) * 6);
+    if (integrator == ORC_RK4) {
+        a[1][0] = 0.5; a[2][1] = 0.5; a[3][2] = 1.0;
+        b[0] = 1.0 / 6.0; b[1] = 2.0 / 6.0; b[2] = 2.0 / 6.0; b[3] = 1.0 / 6.0;
+        return 4;
+    }
+    if (integrator == ORC_RK5_BUTCHER) {
+        a[1][0] = 0.25;
+        a[2][0] = 0.125; a[2][1] = 0.125;
+        a[3][1] = -0.5; a[3][2] = 1.0;
+        a[4][0] = 3.0 / 16.0; a[4][3] = 9.0 / 16.0;
+        a[5][0] = -3.0 / 7.0; a[5][1] = 2.0 / 7.0; a[5][2] = 12.0 / 7.0; a[5][3] = -12.0 / 7.0; a[5][4] = 8.0 / 7.0;
+        b[0] = 7.0 / 90.0; b[2] = 32.0 / 90.0; b[3] = 12.0 / 90.0; b[4] = 32.0 / 90.0; b[5] = 7.0 / 90.0;
+        return 6;
+    }
+    if (integrator == ORC_RK2_MIDPOINT) {
+        a[1][0] = 0.5; b[1] = 1.0;
+        return 2;
+    }
+    a[1][0] = 1.0; b[0] = 0.5; b[1] = 0.5; /* Heun */
+    return 2;
+}
+
+/* out = J_f(x)^T v (f the right-hand side of Eq. LLL without noise), and
+   the parameter gradients <v, df/dJ>, <v, df/dD>, <v, df/dH>, <v, df/dh_i>
+   added into gJ, gD, gH, gh.  With w_i = (df_i/dH_i)^T v_i and
+   u_i = (df_i/ds_i at fixed H)^T v_i:
+     precessional: w = -(s x v) - lambda s x (s x v),
+                   u = H x v - lambda a x v + lambda H x (s x v),  a = s x H
+     slow:         w = -lambda s x (s x v),
+                   u = -lambda a x v + lambda H x (s x v)
+   and out_i = u_i + J sum_{j in nn(i)} w_j + 2D w_iz z. */
+void orc_rhs_vjp(const orc_params *p, const double *x, const double *hsite, const double *v,
+                 double *out, double *gJ, double *gD, double gH[3], double *gh)
+{
+    const int64_t N = (int64_t)p->nx * p->ny * p->nz;
+    double *w = malloc(sizeof(double) * 3 * N);
+    for (int z = 0; z < p->nz; ++z)
+        for (int y = 0; y < p->ny; ++y)
+            for (int xx = 0; xx < p->nx; ++xx) {
+                int64_t i = site_index(p, xx, y, z);
+                double H[3], si[3] = {x[i], x[N + i], x[2 * N + i]}, vi[3] = {v[i], v[N + i], v[2 * N + i]};
+                heff_site(p, x, hsite, xx, y, z, H);
+                double a[3], sv[3], ssv[3], wi[3], Hv[3], av[3], Hsv[3], ui[3];
+                cross(si, H, a);
+                cross(si, vi, sv);
+                cross(si, sv, ssv);
+                cross(H, vi, Hv);
+                cross(a, vi, av);
+                cross(H, sv, Hsv);
+                for (int c = 0; c < 3; ++c) {
+                    if (p->precession) {
+                        wi[c] = -sv[c] - p->lambda * ssv[c];
+                        ui[c] = Hv[c] - p->lambda * av[c] + p->lambda * Hsv[c];
+                    } else {
+                        wi[c] = -p->lambda * ssv[c];
+                        ui[c] = -p->lambda * av[c] + p->lambda * Hsv[c];
+                    }
+                    w[c * N + i] = wi[c];
+                    out[c * N + i] = ui[c];
+                }
+                /* parameter gradients */
+                const int64_t nb[6] = {
+                    site_index(p, xx - 1, y, z), site_index(p, xx + 1, y, z),
+                    site_index(p, xx, y - 1, z), site_index(p, xx, y + 1, z),
+                    site_index(p, xx, y, z - 1), site_index(p, xx, y, z + 1),
+                };
+                for (int c = 0; c < 3; ++c) {
+                    double sum = 0.0;
+                    for (int j = 0; j < 6; ++j) sum += x[c * N + nb[j]];
+                    if (gJ) *gJ += wi[c] * sum;
+                    if (gH) gH[c] += wi[c];
+                    if (gh) gh[c * N + i] += wi[c];
+                }
+                if (gD) *gD += 2.0 * si[2] * wi[2];
+            }
+    for (int z = 0; z < p->nz; ++z)
+        for (int y = 0; y < p->ny; ++y)
+            for (int xx = 0; xx < p->nx; ++xx) {
+                int64_t i = site_index(p, xx, y, z);
+                const int64_t nb[6] = {
+                    site_index(p, xx - 1, y, z), site_index(p, xx + 1, y, z),
+                    site_index(p, xx, y - 1, z), site_index(p, xx, y + 1, z),
+                    site_index(p, xx, y, z - 1), site_index(p, xx, y, z + 1),
+                };
+                for (int c = 0; c < 3; ++c) {
+                    double sum = 0.0;
+                    for (int j = 0; j < 6; ++j) sum += w[c * N + nb[j]];
+                    out[c * N + i] += p->J * sum;
+                }
+                out[2 * N + i] += 2.0 * p->D * w[2 * N + i];
+            }
+    free(w);
+}
+
+/* Adjoint of one full step (integrate, renormalise, pulse k if pulse != 0)
+   taken from state s: lam (3N) holds dL/ds_after on entry and dL/ds_before on
+   exit; parameter gradients accumulate. */
+void orc_step_vjp(const orc_params *p, const double *s, const double *hsite, int pulse, int64_t k,
+                  double *lam, double *gJ, double *gD, double gH[3], double *gh)
+{
+    const int64_t N = (int64_t)p->nx * p->ny * p->nz, len = 3 * N;
+    double A[6][6], B[6];
+    const int S = tableau(p->integrator, A, B);
+    double *X[6], *K[6], *LK[6];
+    for (int j = 0; j < S; ++j) {
+        X[j] = malloc(sizeof(double) * len);
+        K[j] = malloc(sizeof(double) * len);
+        LK[j] = calloc(len, sizeof(double));
+    }
+    double *yv = malloc(sizeof(double) * len), *lx = malloc(sizeof(double) * len);
+    double *vv = malloc(sizeof(double) * len);
+    /* forward recomputation of the stages */
+    for (int j = 0; j < S; ++j) {
+        for (int64_t q = 0; q < len; ++q) {
+            double acc = s[q];
+            for (int l = 0; l < j; ++l) acc += A[j][l] * K[l][q];
+            X[j][q] = acc;
+        }
+        stage(p, X[j], hsite, K[j]);
+    }
+    for (int64_t q = 0; q < len; ++q) {
+        double acc = s[q];
+        for (int j = 0; j < S; ++j) acc += B[j] * K[j][q];
+        yv[q] = acc;
+    }
+    /* pulse: lam <- R^T lam (rotation by -phi) */
+    if (pulse) {
+        const double sigma = orc_pulse_sigma(p);
+        for (int64_t i = 0; i < N; ++i) {
+            double G[3], phi[3], li[3] = {lam[i], lam[N + i], lam[2 * N + i]};
+            orc_noise_gauss(p->seed, i, k, p->replica, G);
+            for (int c = 0; c < 3; ++c) phi[c] = -sigma * G[c];
+            orc_rotate(phi, li);
+            lam[i] = li[0]; lam[N + i] = li[1]; lam[2 * N + i] = li[2];
+        }
+    }
+    /* renormalisation: lam_y = (lam - u (u.lam)) / |y|, u = y/|y| */
+    if (p->renorm) {
+        for (int64_t i = 0; i < N; ++i) {
+            double y3[3] = {yv[i], yv[N + i], yv[2 * N + i]};
+            double n = sqrt(y3[0] * y3[0] + y3[1] * y3[1] + y3[2] * y3[2]);
+            double u[3] = {y3[0] / n, y3[1] / n, y3[2] / n};
+            double ul = u[0] * lam[i] + u[1] * lam[N + i] + u[2] * lam[2 * N + i];
+            for (int c = 0; c < 3; ++c) lam[c * N + i] = (lam[c * N + i] - u[c] * ul) / n;
+        }
+    }
+    /* RK stages in reverse: lam_s starts as lam_y, lam_K_j = b_j lam_y */
+    for (int j = 0; j < S; ++j)
+        for (int64_t q = 0; q < len; ++q) LK[j][q] = B[j] * lam[q];
+    for (int j = S - 1; j >= 0; --j) {
+        for (int64_t q = 0; q < len; ++q) vv[q] = p->dt * LK[j][q];  /* K_j = dt f(x_j) */
+        orc_rhs_vjp(p, X[j], hsite, vv, lx, gJ, gD, gH, gh);
+        for (int64_t q = 0; q < len; ++q) {
+            lam[q] += lx[q];
+            for (int l = 0; l < j; ++l) LK[l][q] += A[j][l] * lx[q];
+        }
+    }
+    for (int j = 0; j < S; ++j) { free(X[j]); free(K[j]); free(LK[j]); }
+    free(yv); free(lx); free(vv);
+}
+
+/* Gradients of L = dLdE E(s_n) + dLdM . M(s_n) after nsteps steps from s0
+   (completed step count n0), all states kept in memory.  Writes
+   *gJ, *gD, gH[3] (sums over the whole path including the explicit final-time
+   terms), gh (3N, nullable) and gs0 (3N, nullable: dL/ds_0). */
+void orc_adjoint(const orc_params *p, const double *s0, const double *hsite, int64_t n0, int64_t nsteps,
+                 int noise, const double dLdM[3], double dLdE, double *gJ, double *gD, double gH[3],
+                 double *gh, double *gs0)
+{
+    const int64_t N = (int64_t)p->nx * p->ny * p->nz, len = 3 * N;
+    double *states = malloc(sizeof(double) * len * (nsteps + 1));
+    memcpy(states, s0, sizeof(double) * len);
+    for (int64_t m = 1; m <= nsteps; ++m) {
+        double *cur = states + m * len;
+        memcpy(cur, states + (m - 1) * len, sizeof(double) * len);
+        int64_t n = n0 + m;
+        orc_integrate(p, cur, hsite);
+        if (p->renorm) orc_renormalise(p, cur);
+        if (noise && orc_is_pulse_step(n, p->R)) orc_pulse(p, cur, orc_pulse_number(n, p->R));
+    }
+    const double *fin = states + nsteps * len;
+    double *lam = malloc(sizeof(double) * len);
+    double *Hf = malloc(sizeof(double) * len);
+    orc_heff(p, fin, hsite, Hf);
+    *gJ = 0.0; *gD = 0.0; gH[0] = gH[1] = gH[2] = 0.0;
+    if (gh) memset(gh, 0, sizeof(double) * len);
+    double bonds = 0.0, sz2 = 0.0, M[3] = {0, 0, 0};
+    for (int z = 0; z < p->nz; ++z)
+        for (int y = 0; y < p->ny; ++y)
+            for (int x = 0; x < p->nx; ++x) {
+                int64_t i = site_index(p, x, y, z);
+                int64_t fwd[3] = {site_index(p, x + 1, y, z), site_index(p, x, y + 1, z),
+                                  site_index(p, x, y, z + 1)};
+                for (int b = 0; b < 3; ++b)
+                    for (int c = 0; c < 3; ++c) bonds += fin[c * N + i] * fin[c * N + fwd[b]];
+                sz2 += fin[2 * N + i] * fin[2 * N + i];
+                for (int c = 0; c < 3; ++c) {
+                    M[c] += fin[c * N + i];
+                    /* dL/ds_n = dLdE (-H_eff/N) + dLdM / N */
+                    lam[c * N + i] = (-dLdE * Hf[c * N + i] + dLdM[c]) / (double)N;
+                    if (gh) gh[c * N + i] += -dLdE * fin[c * N + i] / (double)N;
+                }
+            }
+    /* explicit dependence of E(s_n) on the parameters */
+    *gJ += -dLdE * bonds / (double)N;
+    *gD += -dLdE * sz2 / (double)N;
+    for (int c = 0; c < 3; ++c) gH[c] += -dLdE * M[c] / (double)N;
+    for (int64_t m = nsteps; m >= 1; --m) {
+        int64_t n = n0 + m;
+        int pul = noise && orc_is_pulse_step(n, p->R);
+        orc_step_vjp(p, states + (m - 1) * len, hsite, pul, orc_pulse_number(n, p->R), lam, gJ, gD, gH, gh);
+    }
+    if (gs0) memcpy(gs0, lam, sizeof(double) * len);
+    free(states); free(lam); free(Hf);
+}
