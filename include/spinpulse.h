@@ -156,6 +156,42 @@ int spin_get_step(const spin_lattice* h, int64_t* n);
  */
 int spin_set_step(spin_lattice* h, int64_t n);
 
+/*
+ * Trajectory recording for the adjoint (checkpointing).  From the handle's
+ * current step n0, spin_step_pulse copies the state into `store` every K steps
+ * (slot c holds the state after step n0 + c*K, component-major: 3N values of
+ * the state type), for at most nsteps steps; while recording, steps launch one
+ * by one (no graph replay).  store: caller-owned device memory of at least
+ * spin_record_store_size() bytes, borrowed until spin_record_end.
+ * Errors: SPIN_EINVAL (K < 1, nsteps < 1, null), SPIN_ENOSPACE, SPIN_ECUDA.
+ */
+int spin_record_store_size(const spin_params* p, int32_t K, int64_t nsteps, size_t* bytes);
+int spin_record_begin(spin_lattice* h, int32_t K, int64_t nsteps, void* store, size_t store_bytes);
+int spin_record_end(spin_lattice* h);
+
+/*
+ * Pathwise gradients (noise fixed) of L = dLdE E(s_n) + dLdM . M(s_n) for the
+ * recorded run n0 -> n (the current step), E and M per spin as in
+ * spin_observables.  This is the discrete adjoint of the whole step: RK
+ * stages of Eq. (LLL) (tableaus of the paper's Appendix), renormalisation and
+ * the pulse rotation of Eq. (s_rotation) (transposed: rotation by -phi).
+ * The backward pass restores each checkpoint, recomputes its K steps with
+ * the forward kernels and runs the transposed steps backwards.
+ *   dLdM, dLdE   host seeds of the loss
+ *   workspace    device, >= spin_backward_workspace_size(p, K) bytes, 256-aligned
+ *   gJ, gD, gH   host outputs: dL/dJ, dL/dD, dL/dH (3), including the explicit
+ *                dependence of E(s_n) on the parameters
+ *   g_h_site     nullable device FP64 array of 3N: dL/dh_i (component-major)
+ *   g_s0         nullable device array of 3N (state type): dL/ds_{n0}
+ * Parameter gradients accumulate in FP64; the adjoint state is kept in the
+ * state precision.  Synchronises the stream.
+ * Errors: SPIN_EINVAL (no recording, range mismatch), SPIN_ENOSPACE, SPIN_ECUDA.
+ */
+int spin_backward_workspace_size(const spin_params* p, int32_t K, size_t* bytes);
+int spin_backward(spin_lattice* h, const double dLdM[3], double dLdE, void* workspace,
+                  size_t workspace_bytes, double* gJ, double* gD, double gH[3], void* g_h_site,
+                  void* g_s0);
+
 /* Release the handle's host state and CUDA graphs (not the borrowed arrays). */
 int spin_lattice_destroy(spin_lattice* h);
 

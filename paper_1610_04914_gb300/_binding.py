@@ -49,7 +49,8 @@ class spin_params(ctypes.Structure):
 EXPORTS = [
     "spin_workspace_size", "spin_lattice_create", "spin_step_pulse", "spin_observables",
     "spin_samples", "spin_get_step", "spin_set_step", "spin_lattice_destroy", "spin_strerror",
-    "spin_last_error", "spin_noise_draw", "spin_observables_noalloc",
+    "spin_last_error", "spin_noise_draw", "spin_observables_noalloc", "spin_record_store_size",
+    "spin_record_begin", "spin_record_end", "spin_backward_workspace_size", "spin_backward",
 ]
 
 _lib = None
@@ -81,6 +82,11 @@ def load(path: str = LIB_PATH):
     L.spin_noise_draw.argtypes = [u64, i64, i64, i64, i32, vp, vp, vp]
     d = ctypes.c_double
     L.spin_observables_noalloc.argtypes = [i32, vp, vp, vp, vp, i32, i32, i32, d, d, P(d), vp, vp]
+    L.spin_record_store_size.argtypes = [P(spin_params), i32, i64, P(sz)]
+    L.spin_record_begin.argtypes = [vp, i32, i64, vp, sz]
+    L.spin_record_end.argtypes = [vp]
+    L.spin_backward_workspace_size.argtypes = [P(spin_params), i32, P(sz)]
+    L.spin_backward.argtypes = [vp, P(d), d, vp, sz, P(d), P(d), P(d), vp, vp]
     for name in EXPORTS:
         if name not in ("spin_strerror", "spin_last_error"):
             getattr(L, name).restype = ctypes.c_int

@@ -37,6 +37,11 @@ struct spin_lattice {
     long long samples_read;
     cudaGraphExec_t graph[2];  // one noise interval starting from buffer 0 / 1
     cudaStream_t capture_stream;
+    // trajectory recording for the adjoint
+    bool rec_active;
+    int rec_K;
+    long long rec_n0, rec_max;
+    void* rec_store;
     char err[512];
 };
 
@@ -220,6 +225,60 @@ int capture_interval(spin_lattice* h, int from) {
     return SPIN_OK;
 }
 
+// While recording, copy the current state into checkpoint slot (n-n0)/K
+// whenever n - n0 is a multiple of K within the recorded range.
+int record_if_due(spin_lattice* h) {
+    if (!h->rec_active) return SPIN_OK;
+    const long long d = h->n - h->rec_n0;
+    if (d < 0 || d > h->rec_max || d % h->rec_K != 0) return SPIN_OK;
+    const size_t comp = (size_t)h->elt * (size_t)h->g.N();
+    char* slot = static_cast<char*>(h->rec_store) + (size_t)(d / h->rec_K) * 3 * comp;
+    for (int c = 0; c < 3; ++c)
+        SPIN_CUDA(h, cudaMemcpyAsync(slot + c * comp, h->buf[h->cur][c], comp, cudaMemcpyDeviceToDevice, h->st));
+    return SPIN_OK;
+}
+
+template <typename real>
+int backward_t(spin_lattice* h, const double dLdM[3], double dLdE, void* ws, double* gJ, double* gD,
+                      double gH[3], void* g_h_site, void* g_s0) {
+    AdjointRun<real> A{};
+    A.g = h->g;
+    A.tab = &h->tab;
+    A.K = h->rec_K;
+    A.n0 = h->rec_n0;
+    A.n_end = h->n;
+    A.R = h->p.steps_per_pulse;
+    A.noise = h->p.noise;
+    A.precession = h->p.precession;
+    A.renorm = h->p.renorm;
+    A.seed = h->p.seed;
+    A.replica = (uint64_t)h->p.replica;
+    A.sigma = std::sqrt(2.0 * h->p.lambda * h->p.T * h->p.steps_per_pulse * std::fabs(h->p.dt));
+    A.J = h->p.J;
+    A.D = h->p.D;
+    for (int a = 0; a < 3; ++a) {
+        A.H[a] = h->p.H[a];
+        A.dLdM[a] = dLdM[a];
+    }
+    A.lambda = h->p.lambda;
+    A.dt = h->p.dt;
+    A.h_site = static_cast<const real*>(h->hs[0]);
+    A.store = static_cast<const real*>(h->rec_store);
+    for (int c = 0; c < 3; ++c) A.final_state[c] = static_cast<const real*>(h->buf[h->cur][c]);
+    A.step_template = make_launch<real>(h, 0, false);
+    A.workspace = ws;
+    A.stream = h->st;
+    A.dLdE = dLdE;
+    A.gJ = gJ;
+    A.gD = gD;
+    A.gH = gH;
+    A.g_h = static_cast<double*>(g_h_site);
+    A.g_s0 = static_cast<real*>(g_s0);
+    if (g_h_site) SPIN_CUDA(h, cudaMemsetAsync(g_h_site, 0, sizeof(double) * 3 * (size_t)h->g.N(), h->st));
+    SPIN_CUDA(h, adjoint_run<real>(A));
+    return SPIN_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -311,6 +370,16 @@ int spin_step_pulse(spin_lattice* h, int64_t nsteps) {
     if (!h || nsteps < 0) return SPIN_EINVAL;
     const int R = h->p.steps_per_pulse;
     while (nsteps > 0) {
+        if (h->rec_active) {
+            // recording: single eager steps so every checkpoint step is seen
+            SPIN_CUDA(h, launch_one_step(h, h->cur, h->n + 1, h->st));
+            h->cur ^= 1;
+            h->n += 1;
+            nsteps -= 1;
+            int rc = record_if_due(h);
+            if (rc != SPIN_OK) return rc;
+            continue;
+        }
         if (h->n % R == 0 && nsteps >= R && h->eager_intervals > 0) {
             if (!h->graph[h->cur]) {
                 int rc = capture_interval(h, h->cur);
@@ -384,6 +453,58 @@ int spin_set_step(spin_lattice* h, int64_t n) {
     if (!h || n < 0) return SPIN_EINVAL;
     h->n = n;
     SPIN_CUDA(h, launch_set_counter(h->d_interval, n / h->p.steps_per_pulse, h->st));
+    return SPIN_OK;
+}
+
+int spin_record_store_size(const spin_params* p, int32_t K, int64_t nsteps, size_t* bytes) {
+    if (!bytes || K < 1 || nsteps < 1) return SPIN_EINVAL;
+    int v = validate(p);
+    if (v != SPIN_OK) return v;
+    const size_t comp = (size_t)(p->precision == 64 ? 8 : 4) * (size_t)p->nx * p->ny * p->nz;
+    *bytes = (size_t)((nsteps + K - 1) / K + 1) * 3 * comp;
+    return SPIN_OK;
+}
+
+int spin_record_begin(spin_lattice* h, int32_t K, int64_t nsteps, void* store, size_t store_bytes) {
+    if (!h || !store || K < 1 || nsteps < 1) return SPIN_EINVAL;
+    size_t need = 0;
+    spin_record_store_size(&h->p, K, nsteps, &need);
+    if (store_bytes < need) return SPIN_ENOSPACE;
+    h->rec_active = true;
+    h->rec_K = K;
+    h->rec_n0 = h->n;
+    h->rec_max = nsteps;
+    h->rec_store = store;
+    return record_if_due(h);
+}
+
+int spin_backward_workspace_size(const spin_params* p, int32_t K, size_t* bytes) {
+    if (!bytes || K < 1) return SPIN_EINVAL;
+    int v = validate(p);
+    if (v != SPIN_OK) return v;
+    const Tableau tb = tableau_for(p->integrator);
+    *bytes = adjoint_workspace_bytes(Geom{p->nx, p->ny, p->nz}, p->precision == 64 ? 8 : 4, tb.stages, K);
+    return SPIN_OK;
+}
+
+int spin_backward(spin_lattice* h, const double dLdM[3], double dLdE, void* workspace, size_t workspace_bytes,
+                  double* gJ, double* gD, double gH[3], void* g_h_site, void* g_s0) {
+    if (!h || !dLdM || !gJ || !gD || !gH || !workspace) return SPIN_EINVAL;
+    if (!h->rec_active) return set_err(h, SPIN_EINVAL, "no recorded trajectory (call spin_record_begin first)");
+    if (h->n <= h->rec_n0 || h->n - h->rec_n0 > h->rec_max)
+        return set_err(h, SPIN_EINVAL, "recorded range %lld..%lld does not end at the current step %lld",
+                       h->rec_n0, h->rec_n0 + h->rec_max, h->n);
+    if (reinterpret_cast<uintptr_t>(workspace) % kAlign != 0) return SPIN_EINVAL;
+    size_t need = 0;
+    spin_backward_workspace_size(&h->p, h->rec_K, &need);
+    if (workspace_bytes < need) return SPIN_ENOSPACE;
+    if (h->elt == 4) return backward_t<float>(h, dLdM, dLdE, workspace, gJ, gD, gH, g_h_site, g_s0);
+    return backward_t<double>(h, dLdM, dLdE, workspace, gJ, gD, gH, g_h_site, g_s0);
+}
+
+int spin_record_end(spin_lattice* h) {
+    if (!h) return SPIN_EINVAL;
+    h->rec_active = false;
     return SPIN_OK;
 }
 

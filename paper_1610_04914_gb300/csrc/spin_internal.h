@@ -77,4 +77,32 @@ cudaError_t launch_noise_draw(uint64_t seed, long long k, long long replica, lon
 
 cudaError_t launch_set_counter(long long* d, long long value, cudaStream_t stream);
 
+// Checkpointed discrete adjoint of a recorded run (adjoint.cu).
+template <typename real>
+struct AdjointRun {
+    Geom g;
+    const Tableau* tab;
+    int K;                   // checkpoint interval (steps)
+    long long n0, n_end;     // recorded range: states n0 .. n_end
+    int R, noise, precession, renorm;
+    uint64_t seed, replica;
+    double sigma, J, D, H[3], lambda, dt;
+    const real* h_site;      // component-major 3N or null
+    const real* store;       // checkpoints: state at n0 + c*K, component-major 3N each
+    const real* final_state[3];
+    StepLaunch<real> step_template;  // forward kernels for the recomputation
+    void* workspace;
+    cudaStream_t stream;
+    double dLdM[3];
+    double dLdE;
+    double* gJ;
+    double* gD;
+    double* gH;              // 3 doubles (host)
+    double* g_h;             // device FP64 3N or null
+    real* g_s0;              // device 3N or null
+};
+size_t adjoint_workspace_bytes(const Geom& g, int elt, int stages, int K);
+template <typename real>
+cudaError_t adjoint_run(const AdjointRun<real>& A);
+
 }  // namespace spin

@@ -138,16 +138,51 @@ def spin_observables_noalloc(state: torch.Tensor, J: float, D: float, H, out5: t
                                             float(J), float(D), Hc, out5.data_ptr(), _stream_ptr(stream)))
 
 
+def spin_record_store_size(p: Params, K: int, nsteps: int) -> int:
+    n = ctypes.c_size_t()
+    check(B.load().spin_record_store_size(ctypes.byref(p.c()), int(K), int(nsteps), ctypes.byref(n)))
+    return int(n.value)
+
+
+def spin_record_begin(h, K: int, nsteps: int, store: torch.Tensor) -> None:
+    check(B.load().spin_record_begin(h, int(K), int(nsteps), store.data_ptr(),
+                                     store.numel() * store.element_size()), h)
+
+
+def spin_record_end(h) -> None:
+    check(B.load().spin_record_end(h), h)
+
+
+def spin_backward_workspace_size(p: Params, K: int) -> int:
+    n = ctypes.c_size_t()
+    check(B.load().spin_backward_workspace_size(ctypes.byref(p.c()), int(K), ctypes.byref(n)))
+    return int(n.value)
+
+
+def spin_backward(h, dLdM, dLdE: float, workspace: torch.Tensor, g_h_site: torch.Tensor | None = None,
+                  g_s0: torch.Tensor | None = None):
+    """Returns (dL/dJ, dL/dD, dL/dH[3]); fills g_h_site (FP64, 3N) and g_s0 if given."""
+    dM = (ctypes.c_double * 3)(*[float(v) for v in dLdM])
+    gJ, gD = ctypes.c_double(), ctypes.c_double()
+    gH = (ctypes.c_double * 3)()
+    check(B.load().spin_backward(h, dM, float(dLdE), workspace.data_ptr(),
+                                 workspace.numel() * workspace.element_size(), ctypes.byref(gJ), ctypes.byref(gD), gH,
+                                 g_h_site.data_ptr() if g_h_site is not None else None,
+                                 g_s0.data_ptr() if g_s0 is not None else None), h)
+    return gJ.value, gD.value, [gH[0], gH[1], gH[2]]
+
+
 class Lattice:
     """Owns the device state, the optional per-site field and the workspace of
     one handle.  ``state`` is (3, nz, ny, nx) on the GPU."""
 
     def __init__(self, p: Params, state, h_site=None, device="cuda", stream=None):
         self.p = p
-        self.state = torch.as_tensor(state).to(device=device, dtype=p.dtype).reshape(3, p.nz, p.ny, p.nx).contiguous()
+        # the library updates the state in place: keep a private copy
+        self.state = torch.as_tensor(state).to(device=device, dtype=p.dtype).reshape(3, p.nz, p.ny, p.nx).clone()
         self.h_site = None
         if h_site is not None:
-            self.h_site = torch.as_tensor(h_site).to(device=device, dtype=p.dtype).reshape(3, p.nz, p.ny, p.nx).contiguous()
+            self.h_site = torch.as_tensor(h_site).to(device=device, dtype=p.dtype).reshape(3, p.nz, p.ny, p.nx).clone()
         nbytes = spin_workspace_size(p)
         self.workspace = torch.empty(nbytes // 8 + 32, dtype=torch.float64, device=device)
         self.stream = stream
@@ -171,6 +206,24 @@ class Lattice:
     def set_step(self, n: int) -> None:
         spin_set_step(self.handle, n)
 
+    def record(self, K: int, nsteps: int) -> None:
+        """Checkpoint the trajectory every K steps for the next nsteps steps."""
+        nbytes = spin_record_store_size(self.p, K, nsteps)
+        self.store = torch.empty(nbytes // 8 + 1, dtype=torch.float64, device=self.state.device)
+        self.K = K
+        spin_record_begin(self.handle, K, nsteps, self.store)
+
+    def backward(self, dLdM, dLdE: float, field_grad: bool = True, state_grad: bool = False):
+        """Gradients of dLdE E + dLdM.M of the current state over the recorded
+        run: dict J, D, H and (optionally) h (FP64 (3,nz,ny,nx)) and s0."""
+        p = self.p
+        ws = torch.empty(spin_backward_workspace_size(p, self.K) // 8 + 32, dtype=torch.float64,
+                         device=self.state.device)
+        gh = torch.empty((3, p.nz, p.ny, p.nx), dtype=torch.float64, device=self.state.device) if field_grad else None
+        gs = torch.empty((3, p.nz, p.ny, p.nx), dtype=p.dtype, device=self.state.device) if state_grad else None
+        gJ, gD, gH = spin_backward(self.handle, dLdM, dLdE, ws, gh, gs)
+        return {"J": gJ, "D": gD, "H": gH, "h": gh, "s0": gs}
+
     def close(self) -> None:
         if self.handle is not None:
             spin_lattice_destroy(self.handle)
@@ -181,3 +234,32 @@ class Lattice:
             self.close()
         except Exception:
             pass
+
+
+class SpinRunFn(torch.autograd.Function):
+    """(E, M) of the final state after nsteps pulse-noise steps from s0, with
+    pathwise gradients (noise fixed) w.r.t. J, D and the per-site field h
+    through the library's checkpointed adjoint (checkpoint every K steps)."""
+
+    @staticmethod
+    def forward(ctx, J, D, h_site, s0, p: Params, nsteps: int, K: int):
+        import dataclasses
+        q = dataclasses.replace(p, J=float(J), D=float(D))
+        lat = Lattice(q, s0.detach(), h_site=h_site.detach(), device=s0.device)
+        lat.record(K, nsteps)
+        lat.step(nsteps)
+        M, E = lat.observables()
+        ctx.lat = lat
+        ctx.h_shape = h_site.shape
+        ctx.h_dtype = h_site.dtype
+        return (torch.tensor(E, dtype=torch.float64, device=s0.device),
+                torch.tensor(M, dtype=torch.float64, device=s0.device))
+
+    @staticmethod
+    def backward(ctx, gE, gM):
+        g = ctx.lat.backward(gM.detach().cpu().tolist(), float(gE.detach().cpu()), field_grad=True)
+        ctx.lat.close()
+        dev = gE.device
+        return (torch.tensor(g["J"], dtype=torch.float64, device=dev),
+                torch.tensor(g["D"], dtype=torch.float64, device=dev),
+                g["h"].reshape(ctx.h_shape).to(ctx.h_dtype), None, None, None, None)

@@ -29,7 +29,7 @@ def lib():
 
 def test_header_declares_the_four_calls():
     names = declared_symbols()
-    for n in ("spin_lattice_create", "spin_step_pulse", "spin_observables"):
+    for n in ("spin_lattice_create", "spin_step_pulse", "spin_observables", "spin_backward"):
         assert n in names
 
 

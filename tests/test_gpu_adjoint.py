@@ -1,0 +1,99 @@
+"""GPU checkpointed adjoint (spin_backward through the C-ABI) against the
+oracle's own discrete adjoint on identical inputs and noise.
+
+Tolerances.  FP64 state: the GPU recomputes the same steps, so gradients agree
+to rounding (relative 1e-9 of each gradient's largest entry).  FP32 state and
+adjoint: 20 steps of float rounding in the forward states and the transposed
+stages; relative 1e-3 of the largest entry (measured ~1e-5)."""
+import numpy as np
+import pytest
+import torch
+
+import spin_inputs
+from gpu_helpers import as_input, orc_params
+
+pytestmark = pytest.mark.gpu
+
+
+def _rel(a, b):
+    a, b = np.asarray(a, dtype=float), np.asarray(b, dtype=float)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+CASES = [  # precision, integrator, precession, K
+    (64, 0, 1, 8), (64, 1, 1, 8), (64, 0, 0, 5), (64, 3, 1, 20),
+    (32, 0, 1, 8), (32, 2, 0, 8), (32, 1, 1, 4),
+]
+
+
+@pytest.mark.parametrize("prec,integ,precession,K", CASES)
+def test_adjoint_matches_oracle(gpu, orc, prec, integ, precession, K):
+    shape = (6, 5, 4)
+    nsteps = 20
+    p = gpu.Params(*shape, J=0.9, D=0.25, H=(0.05, -0.1, 0.2), lam=0.1, T=0.8, dt=0.1, R=4, integrator=integ,
+                   precession=precession, seed=12, precision=prec)
+    s0 = spin_inputs.random_spins(*shape, seed=11)
+    hs = spin_inputs.site_fields(*shape, 0.1, seed=13)
+    lat = gpu.Lattice(p, torch.from_numpy(s0), h_site=torch.from_numpy(hs))
+    lat.record(K, nsteps)
+    lat.step(nsteps)
+    dLdM, dLdE = [0.3, -0.2, 0.7], 1.0
+    g = lat.backward(dLdM, dLdE, field_grad=True, state_grad=True)
+    ref = orc.adjoint(orc_params(orc, p), as_input(p, s0), nsteps, dLdM, dLdE, h_site=as_input(p, hs))
+    tol = 1e-9 if prec == 64 else 1e-3
+    assert _rel(g["J"], ref["J"]) < tol
+    assert _rel(g["D"], ref["D"]) < tol
+    assert _rel(g["H"], ref["H"]) < tol
+    assert _rel(g["h"].cpu().numpy(), ref["h"]) < tol
+    assert _rel(g["s0"].double().cpu().numpy(), ref["s0"]) < tol
+
+
+def test_adjoint_full_size_64cubed(gpu, orc):
+    """The 64^3 differentiation workload (J=1, D=0.05, h_i ~ N(0, 0.01^2),
+    lambda=0.05, T=0.8, RK4 dt=0.1, pulses every 10 steps, FP32 forward, FP64
+    gradient accumulation) over 10 steps with checkpoints every 5, against the
+    oracle's adjoint at full size; loss E + |M - m*|^2, m* = (0, 0, 0.5)."""
+    w = spin_inputs.WORKLOADS["adjoint64"]
+    nx, ny, nz = w["n"]
+    p = gpu.Params(nx, ny, nz, J=w["J"], D=w["D"], H=w["H"], lam=w["lam"], T=w["T"], dt=w["dt"], R=w["R"],
+                   seed=w["noise_seed"], precision=32)
+    s0 = spin_inputs.random_spins(nx, ny, nz, seed=w["spin_seed"])
+    hs = spin_inputs.site_fields(nx, ny, nz, w["field_sigma"], seed=w["noise_seed"])
+    nsteps = 10
+    lat = gpu.Lattice(p, torch.from_numpy(s0), h_site=torch.from_numpy(hs))
+    lat.record(5, nsteps)
+    lat.step(nsteps)
+    M, E = lat.observables()
+    dLdM = [2.0 * (M[a] - w["m_target"][a]) for a in range(3)]
+    g = lat.backward(dLdM, 1.0, field_grad=True)
+    ref = orc.adjoint(orc_params(orc, p), as_input(p, s0), nsteps, dLdM, 1.0, h_site=as_input(p, hs))
+    assert _rel(g["J"], ref["J"]) < 1e-3
+    assert _rel(g["D"], ref["D"]) < 1e-3
+    assert _rel(g["H"], ref["H"]) < 1e-3
+    assert _rel(g["h"].cpu().numpy(), ref["h"]) < 1e-3
+
+
+def test_autograd_function(gpu):
+    """SpinRunFn wraps the forward run and spin_backward as a
+    torch.autograd.Function: its gradients equal the direct call."""
+    shape = (8, 8, 8)
+    p = gpu.Params(*shape, J=1.0, D=0.05, H=(0, 0, 0), lam=0.05, T=0.8, dt=0.1, R=10, seed=5, precision=32)
+    s0 = torch.from_numpy(spin_inputs.random_spins(*shape, seed=5)).float().cuda()
+    hs = torch.from_numpy(spin_inputs.site_fields(*shape, 0.01, seed=5)).float().cuda()
+    J = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+    D = torch.tensor(0.05, dtype=torch.float64, requires_grad=True)
+    h = hs.clone().requires_grad_(True)
+    E, M = gpu.SpinRunFn.apply(J, D, h, s0, p, 30, 10)
+    m_target = torch.tensor([0.0, 0.0, 0.5], dtype=torch.float64, device=M.device)
+    loss = E + ((M - m_target) ** 2).sum()
+    loss.backward()
+    lat = gpu.Lattice(p, s0, h_site=hs)
+    lat.record(10, 30)
+    lat.step(30)
+    Md, Ed = lat.observables()
+    assert abs(Ed - E.item()) < 1e-12
+    dLdM = [2.0 * (Md[a] - [0.0, 0.0, 0.5][a]) for a in range(3)]
+    g = lat.backward(dLdM, 1.0)
+    assert abs(J.grad.item() - g["J"]) <= 1e-12 * max(1.0, abs(g["J"]))
+    assert abs(D.grad.item() - g["D"]) <= 1e-12 * max(1.0, abs(g["D"]))
+    assert torch.allclose(h.grad.double(), g["h"].float().double(), rtol=1e-6, atol=1e-9)
