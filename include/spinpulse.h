@@ -211,6 +211,45 @@ int spin_noise_draw(uint64_t seed, int64_t k, int64_t replica, int64_t n_sites,
                     int32_t precision, uint64_t* words, void* gauss, void* cuda_stream);
 
 /*
+ * Batched replicas: nrep independent cubic periodic lattices of sides L[r]
+ * and temperatures T[r] (the paper's ensemble runs "in parallel cycles",
+ * Sec. III.A and Appendix), advanced together by one kernel launch per step
+ * over a table of (replica, tile, z-chunk) work items.  All replicas share
+ * the other spin_params fields (J, D, H, lambda, dt, R, integrator, seed;
+ * nx, ny, nz, replica and path are ignored); replica r draws its noise with
+ * counter word 2 = r, so replica r of a batch reproduces a single lattice
+ * created with replica = r.  FP32 state and chain tableaus (RK4, RK2
+ * midpoint, Heun) only; other requests return SPIN_EUNSUPPORTED.
+ *
+ * State: three caller-owned device float arrays (s_x, s_y, s_z) holding the
+ * replicas back to back, replica r at offset offsets[r] (spin_batch_offsets:
+ * offsets[r] = sum_{q<r} L[q]^3, offsets[nrep] = total), each replica x
+ * fastest.  chunk_planes: z-chunk length of the work items; 0 lets the library
+ * time the candidates 8, 16, 32, 64 on the real tables at create (a short
+ * synchronous autotune, cached per process by the multiset of sizes) and keep
+ * the fastest; spin_batch_tuning reports the choice.
+ * Samples: after steps with n mod R == 0 a record of nrep x 5 doubles
+ * (n, M_x, M_y, M_z, E per replica) goes to a ring of
+ * SPIN_BATCH_SAMPLE_RING records.
+ * Errors as for the single-lattice calls.
+ */
+#define SPIN_BATCH_SAMPLE_RING 512
+typedef struct spin_batch spin_batch;
+int spin_batch_offsets(int32_t nrep, const int32_t* L, int64_t* offsets);
+int spin_batch_workspace_size(const spin_params* p, int32_t nrep, const int32_t* L, size_t* bytes);
+int spin_batch_create(const spin_params* p, int32_t nrep, const int32_t* L, const double* T, void* sx,
+                      void* sy, void* sz, int32_t chunk_planes, void* workspace, size_t workspace_bytes,
+                      void* cuda_stream, spin_batch** out);
+int spin_batch_tuning(const spin_batch* b, int32_t* chunk_planes, int32_t* nitems);
+int spin_batch_step_pulse(spin_batch* b, int64_t nsteps);
+/* current M_x, M_y, M_z, E, non-finite count per replica into host out[5*nrep]; synchronises */
+int spin_batch_observables(spin_batch* b, double* out);
+/* up to max_records unread sample records into host out[max_records*nrep*5]; synchronises */
+int spin_batch_samples(spin_batch* b, double* out, int64_t max_records, int64_t* count);
+int spin_batch_destroy(spin_batch* b);
+const char* spin_batch_last_error(const spin_batch* b);
+
+/*
  * Observables of caller-owned spin arrays with no memory allocation at all.
  * The paper has no counterpart: this entry point serves callers that cannot
  * call cudaMalloc or ask their framework for memory where they need M and E

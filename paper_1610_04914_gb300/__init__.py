@@ -13,3 +13,4 @@ from .lattice import (Lattice, Params, SpinRunFn, spin_backward, spin_backward_w
                       spin_record_store_size,
                       spin_lattice_destroy, spin_noise_draw, spin_observables, spin_observables_noalloc, spin_samples,
                       spin_set_step, spin_step_pulse, spin_workspace_size)
+from .batch import Batch, spin_batch_offsets, spin_batch_workspace_size  # noqa: F401,E402

@@ -22,6 +22,7 @@ SPIN_EUNSUPPORTED = -5
 SPIN_ENOSPACE = -6
 SPIN_SAMPLE_RING = 4096
 SPIN_NOALLOC_MAX_BLOCKS = 1024
+SPIN_BATCH_SAMPLE_RING = 512
 SPIN_NOALLOC_MAX_SITES = 2147483647
 
 RK4, RK5_BUTCHER, RK2_MIDPOINT, HEUN = 0, 1, 2, 3
@@ -51,6 +52,9 @@ EXPORTS = [
     "spin_samples", "spin_get_step", "spin_set_step", "spin_lattice_destroy", "spin_strerror",
     "spin_last_error", "spin_noise_draw", "spin_observables_noalloc", "spin_record_store_size",
     "spin_record_begin", "spin_record_end", "spin_backward_workspace_size", "spin_backward",
+    "spin_batch_offsets", "spin_batch_workspace_size", "spin_batch_create", "spin_batch_tuning",
+    "spin_batch_step_pulse", "spin_batch_observables", "spin_batch_samples", "spin_batch_destroy",
+    "spin_batch_last_error",
 ]
 
 _lib = None
@@ -87,8 +91,18 @@ def load(path: str = LIB_PATH):
     L.spin_record_end.argtypes = [vp]
     L.spin_backward_workspace_size.argtypes = [P(spin_params), i32, P(sz)]
     L.spin_backward.argtypes = [vp, P(d), d, vp, sz, P(d), P(d), P(d), vp, vp]
+    L.spin_batch_offsets.argtypes = [i32, P(i32), P(i64)]
+    L.spin_batch_workspace_size.argtypes = [P(spin_params), i32, P(i32), P(sz)]
+    L.spin_batch_create.argtypes = [P(spin_params), i32, P(i32), P(d), vp, vp, vp, i32, vp, sz, vp, P(vp)]
+    L.spin_batch_tuning.argtypes = [vp, P(i32), P(i32)]
+    L.spin_batch_step_pulse.argtypes = [vp, i64]
+    L.spin_batch_observables.argtypes = [vp, P(d)]
+    L.spin_batch_samples.argtypes = [vp, P(d), i64, P(i64)]
+    L.spin_batch_destroy.argtypes = [vp]
+    L.spin_batch_last_error.argtypes = [vp]
+    L.spin_batch_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
-        if name not in ("spin_strerror", "spin_last_error"):
+        if name not in ("spin_strerror", "spin_last_error", "spin_batch_last_error"):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L

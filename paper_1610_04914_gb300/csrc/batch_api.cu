@@ -1,0 +1,499 @@
+// C-ABI of the batched replicas: many independent cubic periodic lattices of
+// uneven size and temperature (the paper's ensemble averaging in "parallel
+// cycles", Sec. III.A and the Appendix, done as one GPU launch per step).
+// All replicas share J, D, H, lambda, dt, R and the integrator; each has its
+// own side L_r, temperature T_r (pulse angle sqrt(2 lambda T_r Delta t)) and
+// noise stream (replica index r in the counter).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/spinpulse.h"
+#include "spin_internal.h"
+
+using namespace spin;
+
+struct spin_batch {
+    spin_params p;
+    Tableau tab;
+    int nrep;
+    std::vector<int> L;
+    std::vector<double> T;
+    std::vector<int64_t> off;
+    long long ntot;
+    void* buf[2][3];
+    int cur;
+    cudaStream_t st;
+    long long n;
+    long long eager_intervals;
+    // device tables in the workspace
+    BatchRep* reps;
+    BatchItem* items;
+    int nitems;
+    int chunk_planes;      // chosen z-chunk target
+    ObsBlock* oblocks;
+    int* first_block;
+    int nblocks_obs;
+    double* partials;
+    double* out;
+    long long* d_interval;
+    long long* d_sample_count;
+    double* ring;
+    long long samples_read;
+    cudaGraphExec_t graph[2];
+    cudaStream_t capture_stream;
+    std::vector<BatchItem> host_items;
+    std::vector<BatchRep> host_reps;
+    char err[512];
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+size_t al(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+constexpr int kRowsPerObsBlock = 256;
+const int kChunkCandidates[] = {8, 16, 32, 64};
+
+int bset_err(spin_batch* b, int code, const char* fmt, ...) {
+    if (b) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(b->err, sizeof(b->err), fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+#define BATCH_CUDA(b, call)                                                                           \
+    do {                                                                                              \
+        cudaError_t e_ = (call);                                                                      \
+        if (e_ != cudaSuccess) return bset_err(b, SPIN_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+int validate_batch(const spin_params* p, int nrep, const int32_t* L, const double* T) {
+    if (!p || nrep < 1 || !L) return SPIN_EINVAL;
+    if (p->precision != 32) return SPIN_EUNSUPPORTED;
+    const Tableau tb = tableau_for(p->integrator);
+    if (!tb.chain || !(tb.stages == 2 || tb.stages == 4)) return SPIN_EUNSUPPORTED;
+    if (p->steps_per_pulse < 1 || !std::isfinite(p->dt) || p->dt == 0.0 || !(p->lambda >= 0.0)) return SPIN_EINVAL;
+    long long tot = 0;
+    for (int r = 0; r < nrep; ++r) {
+        if (L[r] < 1 || L[r] > 1024) return SPIN_EINVAL;
+        tot += (long long)L[r] * L[r] * L[r];
+        if (T && !(T[r] >= 0.0)) return SPIN_EINVAL;
+    }
+    if (tot >= (1LL << 31)) return SPIN_EINVAL;
+    return SPIN_OK;
+}
+
+std::vector<BatchItem> make_items(const spin_params* p, int nrep, const int32_t* L, int chunk_planes,
+                                  std::vector<int>* tz_out) {
+    const int S = tableau_for(p->integrator).stages;
+    const int ox = patch_out_x(S), oy = patch_out_y(S);
+    std::vector<std::pair<int, BatchItem>> v;
+    tz_out->assign(nrep, 1);
+    for (int r = 0; r < nrep; ++r) {
+        const int chunks = std::max(1, (L[r] + chunk_planes - 1) / chunk_planes);
+        const int tz = (L[r] + chunks - 1) / chunks;
+        (*tz_out)[r] = tz;
+        const int tx = (L[r] + ox - 1) / ox, ty = (L[r] + oy - 1) / oy;
+        const int used = (L[r] + tz - 1) / tz;
+        for (int bz = 0; bz < used; ++bz)
+            for (int by = 0; by < ty; ++by)
+                for (int bx = 0; bx < tx; ++bx) v.push_back({tz + 2 * S - 2, BatchItem{r, (short)bx, (short)by, bz}});
+    }
+    // most expensive items first: the block scheduler then balances the tail
+    std::stable_sort(v.begin(), v.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+    std::vector<BatchItem> items;
+    items.reserve(v.size());
+    for (auto& e : v) items.push_back(e.second);
+    return items;
+}
+
+int max_items(const spin_params* p, int nrep, const int32_t* L) {
+    size_t m = 0;
+    std::vector<int> tz;
+    for (int c : kChunkCandidates) m = std::max(m, make_items(p, nrep, L, c, &tz).size());
+    return (int)m;
+}
+
+int obs_blocks(int nrep, const int32_t* L, std::vector<ObsBlock>* blocks, std::vector<int>* first) {
+    blocks->clear();
+    first->assign(nrep + 1, 0);
+    for (int r = 0; r < nrep; ++r) {
+        (*first)[r] = (int)blocks->size();
+        const int rows = L[r] * L[r];
+        for (int r0 = 0; r0 < rows; r0 += kRowsPerObsBlock)
+            blocks->push_back(ObsBlock{r, r0, std::min(kRowsPerObsBlock, rows - r0)});
+    }
+    (*first)[nrep] = (int)blocks->size();
+    return (int)blocks->size();
+}
+
+struct BLayout {
+    size_t alt[3], reps, items, oblocks, first, partials, out, interval, count, ring, total;
+};
+
+BLayout blayout(const spin_params* p, int nrep, const int32_t* L) {
+    BLayout b{};
+    long long tot = 0;
+    for (int r = 0; r < nrep; ++r) tot += (long long)L[r] * L[r] * L[r];
+    std::vector<ObsBlock> ob;
+    std::vector<int> fb;
+    const int nob = obs_blocks(nrep, L, &ob, &fb);
+    size_t off = 0;
+    for (int c = 0; c < 3; ++c) {
+        b.alt[c] = off;
+        off += al(sizeof(float) * (size_t)tot);
+    }
+    b.reps = off;
+    off += al(sizeof(BatchRep) * (size_t)nrep);
+    b.items = off;
+    off += al(sizeof(BatchItem) * (size_t)max_items(p, nrep, L));
+    b.oblocks = off;
+    off += al(sizeof(ObsBlock) * (size_t)nob);
+    b.first = off;
+    off += al(sizeof(int) * (size_t)(nrep + 1));
+    b.partials = off;
+    off += al(sizeof(double) * 5 * (size_t)nob);
+    b.out = off;
+    off += al(sizeof(double) * 5 * (size_t)nrep);
+    b.interval = off;
+    off += al(sizeof(long long));
+    b.count = off;
+    off += al(sizeof(long long));
+    b.ring = off;
+    off += al(sizeof(double) * 5 * (size_t)nrep * SPIN_BATCH_SAMPLE_RING);
+    b.total = off;
+    return b;
+}
+
+StepLaunch<float> batch_launch_args(spin_batch* b, int from, bool pulse, cudaStream_t st) {
+    StepLaunch<float> Ls{};
+    for (int c = 0; c < 3; ++c) {
+        Ls.in[c] = static_cast<const float*>(b->buf[from][c]);
+        Ls.out[c] = static_cast<float*>(b->buf[from ^ 1][c]);
+        Ls.hs[c] = nullptr;
+    }
+    Ls.g = Geom{1, 1, 1};
+    Ls.ph.J = (float)b->p.J;
+    Ls.ph.twoD = (float)(2.0 * b->p.D);
+    for (int a = 0; a < 3; ++a) Ls.ph.H[a] = (float)b->p.H[a];
+    Ls.ph.lambda = (float)b->p.lambda;
+    Ls.dt = b->p.dt;
+    Ls.tab = &b->tab;
+    Ls.precession = b->p.precession;
+    Ls.renorm = b->p.renorm;
+    Ls.pulse = pulse ? 1 : 0;
+    Ls.seed = b->p.seed;
+    Ls.d_interval = b->d_interval;
+    Ls.stream = st;
+    return Ls;
+}
+
+Phys<double> bphys(const spin_batch* b) {
+    Phys<double> ph{};
+    ph.J = b->p.J;
+    ph.twoD = 2.0 * b->p.D;
+    for (int a = 0; a < 3; ++a) ph.H[a] = b->p.H[a];
+    ph.lambda = b->p.lambda;
+    return ph;
+}
+
+cudaError_t batch_observe(spin_batch* b, int buf, bool sample, cudaStream_t st) {
+    const float* s[3] = {(const float*)b->buf[buf][0], (const float*)b->buf[buf][1], (const float*)b->buf[buf][2]};
+    return launch_observables_batch(s, b->reps, b->oblocks, b->nblocks_obs, b->first_block, b->nrep, bphys(b),
+                                    b->partials, b->out, sample ? b->ring : nullptr, SPIN_BATCH_SAMPLE_RING,
+                                    b->d_interval, b->d_sample_count, b->p.steps_per_pulse, st);
+}
+
+cudaError_t batch_one_step(spin_batch* b, int from, long long n_next, cudaStream_t st) {
+    const int R = b->p.steps_per_pulse;
+    const bool pulse = b->p.noise && (n_next % R) == (R / 2);
+    cudaError_t e = launch_step_patch_batch(batch_launch_args(b, from, pulse, st), b->items, b->nitems, b->reps);
+    if (e != cudaSuccess) return e;
+    if (n_next % R == 0) e = batch_observe(b, from ^ 1, true, st);
+    return e;
+}
+
+int upload_tables(spin_batch* b, int chunk_planes) {
+    std::vector<int> tz;
+    b->host_items = make_items(&b->p, b->nrep, b->L.data(), chunk_planes, &tz);
+    b->nitems = (int)b->host_items.size();
+    const int S = b->tab.stages;
+    (void)S;
+    b->host_reps.assign(b->nrep, BatchRep{});
+    const double Dt = b->p.steps_per_pulse * std::fabs(b->p.dt);
+    for (int r = 0; r < b->nrep; ++r) {
+        b->host_reps[r].off = b->off[r];
+        b->host_reps[r].L = b->L[r];
+        b->host_reps[r].tz = tz[r];
+        b->host_reps[r].sigma = (float)std::sqrt(2.0 * b->p.lambda * b->T[r] * Dt);
+    }
+    BATCH_CUDA(b, cudaMemcpy(b->items, b->host_items.data(), sizeof(BatchItem) * b->host_items.size(),
+                             cudaMemcpyHostToDevice));
+    BATCH_CUDA(b, cudaMemcpy(b->reps, b->host_reps.data(), sizeof(BatchRep) * b->host_reps.size(),
+                             cudaMemcpyHostToDevice));
+    b->chunk_planes = chunk_planes;
+    return SPIN_OK;
+}
+
+std::mutex g_tune_mutex;
+std::map<std::string, int> g_tune_cache;
+
+std::string tune_key(const spin_batch* b) {
+    std::vector<int> Ls(b->L);
+    std::sort(Ls.begin(), Ls.end());
+    std::string k = "p" + std::to_string(b->p.precision) + "i" + std::to_string(b->p.integrator) + "L";
+    for (int v : Ls) k += std::to_string(v) + ",";
+    return k;
+}
+
+// Time each z-chunk candidate on the real tables (input buffer 0 -> buffer 1,
+// no pulse, so the caller's state is untouched) and keep the fastest.
+int autotune(spin_batch* b, int* best) {
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto it = g_tune_cache.find(tune_key(b));
+        if (it != g_tune_cache.end()) {
+            *best = it->second;
+            return SPIN_OK;
+        }
+    }
+    cudaEvent_t e0, e1;
+    BATCH_CUDA(b, cudaEventCreate(&e0));
+    BATCH_CUDA(b, cudaEventCreate(&e1));
+    float best_ms = 1e30f;
+    *best = kChunkCandidates[0];
+    for (int c : kChunkCandidates) {
+        int rc = upload_tables(b, c);
+        if (rc != SPIN_OK) return rc;
+        StepLaunch<float> Ls = batch_launch_args(b, 0, false, b->st);
+        BATCH_CUDA(b, launch_step_patch_batch(Ls, b->items, b->nitems, b->reps));
+        float ms_min = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+            BATCH_CUDA(b, cudaEventRecord(e0, b->st));
+            BATCH_CUDA(b, launch_step_patch_batch(Ls, b->items, b->nitems, b->reps));
+            BATCH_CUDA(b, cudaEventRecord(e1, b->st));
+            BATCH_CUDA(b, cudaEventSynchronize(e1));
+            float ms = 0;
+            BATCH_CUDA(b, cudaEventElapsedTime(&ms, e0, e1));
+            ms_min = std::min(ms_min, ms);
+        }
+        if (ms_min < best_ms) {
+            best_ms = ms_min;
+            *best = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune_cache[tune_key(b)] = *best;
+    return SPIN_OK;
+}
+
+int capture_batch_interval(spin_batch* b, int from) {
+    if (!b->capture_stream) BATCH_CUDA(b, cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking));
+    cudaStream_t cs = b->capture_stream;
+    BATCH_CUDA(b, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    int bb = from;
+    cudaError_t e = cudaSuccess;
+    for (int q = 1; q <= b->p.steps_per_pulse && e == cudaSuccess; ++q) {
+        e = batch_one_step(b, bb, q, cs);
+        bb ^= 1;
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return bset_err(b, SPIN_ECUDA, "batch interval capture: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    cudaError_t e3 = cudaGraphInstantiate(&b->graph[from], g, 0);
+    cudaGraphDestroy(g);
+    if (e3 != cudaSuccess) return bset_err(b, SPIN_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e3));
+    return SPIN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int spin_batch_offsets(int32_t nrep, const int32_t* L, int64_t* offsets) {
+    if (nrep < 1 || !L || !offsets) return SPIN_EINVAL;
+    int64_t o = 0;
+    for (int r = 0; r < nrep; ++r) {
+        if (L[r] < 1) return SPIN_EINVAL;
+        offsets[r] = o;
+        o += (int64_t)L[r] * L[r] * L[r];
+    }
+    offsets[nrep] = o;
+    return SPIN_OK;
+}
+
+int spin_batch_workspace_size(const spin_params* p, int32_t nrep, const int32_t* L, size_t* bytes) {
+    if (!bytes) return SPIN_EINVAL;
+    int v = validate_batch(p, nrep, L, nullptr);
+    if (v != SPIN_OK) return v;
+    *bytes = blayout(p, nrep, L).total;
+    return SPIN_OK;
+}
+
+int spin_batch_create(const spin_params* p, int32_t nrep, const int32_t* L, const double* T, void* sx, void* sy,
+                      void* sz, int32_t chunk_planes, void* workspace, size_t workspace_bytes, void* cuda_stream,
+                      spin_batch** out) {
+    if (!out) return SPIN_EINVAL;
+    *out = nullptr;
+    int v = validate_batch(p, nrep, L, T);
+    if (v != SPIN_OK) return v;
+    if (!T || !sx || !sy || !sz || !workspace || reinterpret_cast<uintptr_t>(workspace) % kAlign) return SPIN_EINVAL;
+    if (chunk_planes < 0) return SPIN_EINVAL;
+    const BLayout Lo = blayout(p, nrep, L);
+    if (workspace_bytes < Lo.total) return SPIN_ENOSPACE;
+    spin_batch* b = new (std::nothrow) spin_batch();
+    if (!b) return SPIN_EINVAL;
+    b->p = *p;
+    b->tab = tableau_for(p->integrator);
+    b->nrep = nrep;
+    b->L.assign(L, L + nrep);
+    b->T.assign(T, T + nrep);
+    b->off.resize(nrep + 1);
+    spin_batch_offsets(nrep, L, b->off.data());
+    b->ntot = b->off[nrep];
+    b->buf[0][0] = sx;
+    b->buf[0][1] = sy;
+    b->buf[0][2] = sz;
+    char* ws = static_cast<char*>(workspace);
+    for (int c = 0; c < 3; ++c) b->buf[1][c] = ws + Lo.alt[c];
+    b->st = static_cast<cudaStream_t>(cuda_stream);
+    b->reps = reinterpret_cast<BatchRep*>(ws + Lo.reps);
+    b->items = reinterpret_cast<BatchItem*>(ws + Lo.items);
+    b->oblocks = reinterpret_cast<ObsBlock*>(ws + Lo.oblocks);
+    b->first_block = reinterpret_cast<int*>(ws + Lo.first);
+    b->partials = reinterpret_cast<double*>(ws + Lo.partials);
+    b->out = reinterpret_cast<double*>(ws + Lo.out);
+    b->d_interval = reinterpret_cast<long long*>(ws + Lo.interval);
+    b->d_sample_count = reinterpret_cast<long long*>(ws + Lo.count);
+    b->ring = reinterpret_cast<double*>(ws + Lo.ring);
+    int rc = SPIN_OK;
+    do {
+        if (prepare_step_kernels<float>() != cudaSuccess) {
+            rc = SPIN_ECUDA;
+            break;
+        }
+        std::vector<ObsBlock> ob;
+        std::vector<int> fb;
+        b->nblocks_obs = obs_blocks(nrep, L, &ob, &fb);
+        if (cudaMemcpy(b->oblocks, ob.data(), sizeof(ObsBlock) * ob.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(b->first_block, fb.data(), sizeof(int) * fb.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemsetAsync(b->d_interval, 0, sizeof(long long), b->st) != cudaSuccess ||
+            cudaMemsetAsync(b->d_sample_count, 0, sizeof(long long), b->st) != cudaSuccess) {
+            rc = SPIN_ECUDA;
+            break;
+        }
+        int chosen = chunk_planes;
+        if (chosen == 0) {
+            if ((rc = upload_tables(b, kChunkCandidates[0])) != SPIN_OK) break;
+            if ((rc = autotune(b, &chosen)) != SPIN_OK) break;
+        }
+        rc = upload_tables(b, chosen);
+    } while (0);
+    if (rc != SPIN_OK) {
+        delete b;
+        return rc;
+    }
+    *out = b;
+    return SPIN_OK;
+}
+
+int spin_batch_tuning(const spin_batch* b, int32_t* chunk_planes, int32_t* nitems) {
+    if (!b) return SPIN_EINVAL;
+    if (chunk_planes) *chunk_planes = b->chunk_planes;
+    if (nitems) *nitems = b->nitems;
+    return SPIN_OK;
+}
+
+int spin_batch_step_pulse(spin_batch* b, int64_t nsteps) {
+    if (!b || nsteps < 0) return SPIN_EINVAL;
+    const int R = b->p.steps_per_pulse;
+    while (nsteps > 0) {
+        if (b->n % R == 0 && nsteps >= R && b->eager_intervals > 0) {
+            if (!b->graph[b->cur]) {
+                int rc = capture_batch_interval(b, b->cur);
+                if (rc != SPIN_OK) return rc;
+            }
+            BATCH_CUDA(b, cudaGraphLaunch(b->graph[b->cur], b->st));
+            b->n += R;
+            if (R & 1) b->cur ^= 1;
+            nsteps -= R;
+            continue;
+        }
+        const bool interval_start = b->n % R == 0 && nsteps >= R;
+        const int steps = interval_start ? R : 1;
+        for (int q = 0; q < steps; ++q) {
+            BATCH_CUDA(b, batch_one_step(b, b->cur, b->n + 1, b->st));
+            b->cur ^= 1;
+            b->n += 1;
+        }
+        nsteps -= steps;
+        if (interval_start) b->eager_intervals++;
+    }
+    if (b->cur == 1) {
+        const size_t bytes = sizeof(float) * (size_t)b->ntot;
+        for (int c = 0; c < 3; ++c)
+            BATCH_CUDA(b, cudaMemcpyAsync(b->buf[0][c], b->buf[1][c], bytes, cudaMemcpyDeviceToDevice, b->st));
+        b->cur = 0;
+    }
+    return SPIN_OK;
+}
+
+int spin_batch_observables(spin_batch* b, double* out) {
+    if (!b || !out) return SPIN_EINVAL;
+    BATCH_CUDA(b, batch_observe(b, b->cur, false, b->st));
+    BATCH_CUDA(b, cudaMemcpyAsync(out, b->out, sizeof(double) * 5 * (size_t)b->nrep, cudaMemcpyDeviceToHost, b->st));
+    BATCH_CUDA(b, cudaStreamSynchronize(b->st));
+    for (int r = 0; r < b->nrep; ++r)
+        if (out[5 * r + 4] != 0.0) return bset_err(b, SPIN_ENONFINITE, "replica %d has non-finite spins", r);
+    return SPIN_OK;
+}
+
+int spin_batch_samples(spin_batch* b, double* out, int64_t max_records, int64_t* count) {
+    if (!b || !count || max_records < 0 || (max_records > 0 && !out)) return SPIN_EINVAL;
+    long long total = 0;
+    BATCH_CUDA(b, cudaMemcpyAsync(&total, b->d_sample_count, sizeof(total), cudaMemcpyDeviceToHost, b->st));
+    BATCH_CUDA(b, cudaStreamSynchronize(b->st));
+    long long first = b->samples_read;
+    if (total - first > SPIN_BATCH_SAMPLE_RING) first = total - SPIN_BATCH_SAMPLE_RING;
+    if (total - first > max_records) first = total - max_records;
+    const long long n = total - first;
+    const size_t rec = sizeof(double) * 5 * (size_t)b->nrep;
+    for (long long q = 0; q < n; ++q) {
+        const long long slot = (first + q) % SPIN_BATCH_SAMPLE_RING;
+        BATCH_CUDA(b, cudaMemcpyAsync(out + q * 5 * b->nrep, b->ring + slot * 5 * b->nrep, rec, cudaMemcpyDeviceToHost,
+                                      b->st));
+    }
+    BATCH_CUDA(b, cudaStreamSynchronize(b->st));
+    b->samples_read = total;
+    *count = n;
+    return SPIN_OK;
+}
+
+int spin_batch_destroy(spin_batch* b) {
+    if (!b) return SPIN_EINVAL;
+    for (int q = 0; q < 2; ++q)
+        if (b->graph[q]) cudaGraphExecDestroy(b->graph[q]);
+    if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+    delete b;
+    return SPIN_OK;
+}
+
+const char* spin_batch_last_error(const spin_batch* b) { return b ? b->err : "null handle"; }
+
+}  // extern "C"

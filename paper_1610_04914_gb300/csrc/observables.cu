@@ -134,6 +134,109 @@ __global__ void __launch_bounds__(kObsThreads) k_obs_final(const double* __restr
     }
 }
 
+// Batched replicas: the same row-wise reduction, each block on a row range
+// of one replica; the final pass gives one record per replica.
+__global__ void __launch_bounds__(kObsThreads) k_obs_batch_partial(const float* __restrict__ sx, const float* __restrict__ sy,
+                                                                   const float* __restrict__ sz,
+                                                                   const BatchRep* __restrict__ reps,
+                                                                   const ObsBlock* __restrict__ blocks, double J, double D,
+                                                                   double H0, double H1, double H2,
+                                                                   double* __restrict__ partials) {
+    const ObsBlock ob = blocks[blockIdx.x];
+    const BatchRep rp = reps[ob.rep];
+    const int L = rp.L;
+    const long long P = (long long)L * L;
+    const float* ax = sx + rp.off;
+    const float* ay = sy + rp.off;
+    const float* az = sz + rp.off;
+    const int lane = threadIdx.x & 31;
+    double m0 = 0, m1 = 0, m2 = 0, e = 0, bad = 0;
+    const float Jr = (float)J, Dr = (float)D, H0r = (float)H0, H1r = (float)H1, H2r = (float)H2;
+    for (int row = ob.row0 + (threadIdx.x >> 5); row < ob.row0 + ob.nrows; row += (blockDim.x >> 5)) {
+        const int y = row % L, z = row / L;
+        const long long rb = (long long)z * P + (long long)y * L;
+        const long long rby = (long long)z * P + (long long)(y + 1 == L ? 0 : y + 1) * L;
+        const long long rbz = (long long)(z + 1 == L ? 0 : z + 1) * P + (long long)y * L;
+        float rm0 = 0, rm1 = 0, rm2 = 0, re = 0;
+        int rbad = 0;
+        for (int x = lane; x < L; x += 32) {
+            const long long i = rb + x, ix = rb + (x + 1 == L ? 0 : x + 1), iy = rby + x, iz = rbz + x;
+            const float a = ax[i], b = ay[i], c = az[i];
+            if (!isfinite(a) || !isfinite(b) || !isfinite(c)) rbad += 1;
+            rm0 += a;
+            rm1 += b;
+            rm2 += c;
+            const float bond = a * (ax[ix] + ax[iy] + ax[iz]) + b * (ay[ix] + ay[iy] + ay[iz]) + c * (az[ix] + az[iy] + az[iz]);
+            re += -Jr * bond - Dr * c * c - (H0r * a + H1r * b + H2r * c);
+        }
+        m0 += (double)rm0;
+        m1 += (double)rm1;
+        m2 += (double)rm2;
+        e += (double)re;
+        bad += (double)rbad;
+    }
+    __shared__ double red[kObsThreads / 32][5];
+    m0 = warp_sum(m0);
+    m1 = warp_sum(m1);
+    m2 = warp_sum(m2);
+    e = warp_sum(e);
+    bad = warp_sum(bad);
+    const int w = threadIdx.x >> 5;
+    if (lane == 0) {
+        red[w][0] = m0;
+        red[w][1] = m1;
+        red[w][2] = m2;
+        red[w][3] = e;
+        red[w][4] = bad;
+    }
+    __syncthreads();
+    if (threadIdx.x < 5) {
+        double acc = 0;
+        for (int q = 0; q < kObsThreads / 32; ++q) acc += red[q][threadIdx.x];
+        partials[(long long)blockIdx.x * 5 + threadIdx.x] = acc;
+    }
+}
+
+__global__ void __launch_bounds__(kObsThreads) k_obs_batch_final(const double* __restrict__ partials,
+                                                                 const int* __restrict__ first_block,
+                                                                 const BatchRep* __restrict__ reps, int nrep,
+                                                                 double* __restrict__ out, double* __restrict__ ring,
+                                                                 int ring_len, long long* __restrict__ interval,
+                                                                 long long* __restrict__ sample_count, int R) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const long long m = ring ? *interval : 0;
+    const long long slot = ring ? (*sample_count % ring_len) : 0;
+    for (int r = w; r < nrep; r += blockDim.x >> 5) {
+        double acc[5] = {0, 0, 0, 0, 0};
+        for (int b = first_block[r] + lane; b < first_block[r + 1]; b += 32)
+            for (int q = 0; q < 5; ++q) acc[q] += partials[(long long)b * 5 + q];
+        for (int q = 0; q < 5; ++q) acc[q] = warp_sum(acc[q]);
+        if (lane == 0) {
+            const double L = (double)reps[r].L;
+            const double invN = 1.0 / (L * L * L);
+            double* o = out + (long long)r * 5;
+            o[0] = acc[0] * invN;
+            o[1] = acc[1] * invN;
+            o[2] = acc[2] * invN;
+            o[3] = acc[3] * invN;
+            o[4] = acc[4];
+            if (ring) {
+                double* rec = ring + (slot * nrep + r) * 5;
+                rec[0] = (double)((m + 1) * (long long)R);
+                rec[1] = o[0];
+                rec[2] = o[1];
+                rec[3] = o[2];
+                rec[4] = o[3];
+            }
+        }
+    }
+    __syncthreads();
+    if (ring && threadIdx.x == 0) {
+        *interval = m + 1;
+        *sample_count = *sample_count + 1;
+    }
+}
+
 }  // namespace
 
 int observables_blocks(Geom g) {
@@ -157,6 +260,17 @@ cudaError_t launch_observables(const real* s[3], const real* hs[3], Geom g, Phys
                                                                         (double)ph.H[1], (double)ph.H[2], partials);
     k_obs_final<<<1, kObsThreads, 0, stream>>>(partials, nblocks, g.N(), out5, sample_ring, ring, d_interval,
                                                d_sample_count, R);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_observables_batch(const float* s[3], const BatchRep* reps, const ObsBlock* blocks, int nblocks,
+                                     const int* first_block, int nrep, Phys<double> ph, double* partials,
+                                     double* out, double* ring, int ring_len, long long* d_interval,
+                                     long long* d_sample_count, int R, cudaStream_t stream) {
+    k_obs_batch_partial<<<nblocks, kObsThreads, 0, stream>>>(s[0], s[1], s[2], reps, blocks, ph.J, 0.5 * ph.twoD,
+                                                             ph.H[0], ph.H[1], ph.H[2], partials);
+    k_obs_batch_final<<<1, kObsThreads, 0, stream>>>(partials, first_block, reps, nrep, out, ring, ring_len, d_interval,
+                                                     d_sample_count, R);
     return cudaGetLastError();
 }
 

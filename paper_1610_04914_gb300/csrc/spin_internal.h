@@ -57,9 +57,39 @@ cudaError_t launch_step(const StepLaunch<real>& L);
 // (call once per device before launching or capturing).
 template <typename real>
 cudaError_t prepare_step_kernels();
-// FP32 fused step with 2x2 register patches (chain tableaus, 2 or 4 stages).
+// FP32 fused step with register patches (chain tableaus, 2 or 4 stages).
 cudaError_t launch_step_patch(const StepLaunch<float>& L);
 cudaError_t prepare_patch_kernels();
+int patch_out_x(int stages);   // output columns per CTA tile along x
+int patch_out_y(int stages);   // ... along y
+
+// Batched replicas (cubic periodic lattices, one concatenated SoA state).
+struct BatchItem {
+    int rep;
+    short bx, by;
+    int bz;
+};
+struct BatchRep {
+    long long off;   // first site of the replica in the concatenated arrays
+    int L;           // side
+    int tz;          // z chunk (planes)
+    float sigma;     // pulse angle scale sqrt(2 lambda T_r Delta t)
+    int pad;
+};
+cudaError_t launch_step_patch_batch(const StepLaunch<float>& L, const BatchItem* items, int nitems,
+                                    const BatchRep* reps);
+
+// Batched observables: block b reduces rows [row0, row0+nrows) of replica rep;
+// blocks of one replica are contiguous; first_block has nrep+1 entries.
+struct ObsBlock {
+    int rep;
+    int row0;
+    int nrows;
+};
+cudaError_t launch_observables_batch(const float* s[3], const BatchRep* reps, const ObsBlock* blocks, int nblocks,
+                                     const int* first_block, int nrep, Phys<double> ph, double* partials,
+                                     double* out, double* ring, int ring_len, long long* d_interval,
+                                     long long* d_sample_count, int R, cudaStream_t stream);
 
 // FP64 observables: per-block partials, then a one-block deterministic sum.
 // out5 = (M_x, M_y, M_z, E, nonfinite count); if sample_ring != null the

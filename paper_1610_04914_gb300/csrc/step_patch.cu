@@ -284,11 +284,10 @@ __device__ __forceinline__ void patch_iteration(const PatchArgs& a, PRings<S, HS
     }
 }
 
+// One CTA's tile: columns (bx, by) of the x-y tiling, z chunk bz.
 template <int S, bool PREC, bool HSITE, bool PULSE>
-__global__ void __launch_bounds__(kPT* PatchShape<S>::TY, 1) k_step_patch(PatchArgs a) {
+__device__ __forceinline__ void patch_tile(const PatchArgs& a, int bx, int by, int bz, float* __restrict__ sh) {
     constexpr int PY = PatchShape<S>::PY, ROWS = PatchShape<S>::PY * PatchShape<S>::TY;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float* sh = reinterpret_cast<float*>(smem_raw);
     float* stg = sh + 2 * S * 3 * ROWS * kRS;
     const int tid = threadIdx.y * kPT + threadIdx.x;
     PThread<PY> th;
@@ -300,17 +299,17 @@ __global__ void __launch_bounds__(kPT* PatchShape<S>::TY, 1) k_step_patch(PatchA
 #pragma unroll
     for (int rr = 0; rr < PY; ++rr) {
         const int cy = PY * th.ty + rr;
-        const int gyu = (int)blockIdx.y * OUTY - S + cy;
+        const int gyu = by * OUTY - S + cy;
         const int gy = wrapi(gyu, a.ny);
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
             const int cx = 2 * th.tx + e;
-            const int gxu = (int)blockIdx.x * OUTX - S + cx;
+            const int gxu = bx * OUTX - S + cx;
             th.col[rr][e] = gy * a.nx + wrapi(gxu, a.nx);
             th.out[rr][e] = cx >= S && cx < kPC - S && cy >= S && cy < ROWS - S && gxu < a.nx && gyu < a.ny;
         }
     }
-    const int z0 = (int)blockIdx.z * a.tz;
+    const int z0 = bz * a.tz;
     const int t0 = z0 - 2 * S + 2;
     const long long k = PULSE ? *a.interval : 0;
 
@@ -351,7 +350,39 @@ __global__ void __launch_bounds__(kPT* PatchShape<S>::TY, 1) k_step_patch(PatchA
     if (i < a.n_iter) patch_iteration<S, PREC, HSITE, PULSE, 0>(a, r, sh, stg, th, i + 0, t0, z0, k, tid);
     if (i + 1 < a.n_iter) patch_iteration<S, PREC, HSITE, PULSE, 1>(a, r, sh, stg, th, i + 1, t0, z0, k, tid);
     if (i + 2 < a.n_iter) patch_iteration<S, PREC, HSITE, PULSE, 2>(a, r, sh, stg, th, i + 2, t0, z0, k, tid);
-    cp_async_wait<0>();   // no copy may land in shared memory after the CTA exits
+    cp_async_wait<0>();   // no copy may land in shared memory after the tile is done
+}
+
+template <int S, bool PREC, bool HSITE, bool PULSE>
+__global__ void __launch_bounds__(kPT* PatchShape<S>::TY, 1) k_step_patch(PatchArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    patch_tile<S, PREC, HSITE, PULSE>(a, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z,
+                                      reinterpret_cast<float*>(smem_raw));
+}
+
+// Batched replicas: one CTA per work item (replica, x tile, y tile, z chunk)
+// of a table sorted by cost; each replica is a cubic periodic lattice of side
+// L at its own offset in the concatenated arrays, with its own pulse angle
+// scale (temperature) and its index as the noise counter's replica word.
+template <int S, bool PREC, bool PULSE>
+__global__ void __launch_bounds__(kPT* PatchShape<S>::TY, 1)
+    k_step_patch_batch(PatchArgs base, const BatchItem* __restrict__ items, const BatchRep* __restrict__ reps) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const BatchItem it = items[blockIdx.x];
+    const BatchRep rp = reps[it.rep];
+    PatchArgs a = base;
+    a.in0 += rp.off;
+    a.in1 += rp.off;
+    a.in2 += rp.off;
+    a.out0 += rp.off;
+    a.out1 += rp.off;
+    a.out2 += rp.off;
+    a.nx = a.ny = a.nz = rp.L;
+    a.tz = rp.tz;
+    a.n_iter = rp.tz + 2 * S - 2;
+    a.sigma = rp.sigma;
+    a.replica = (uint64_t)it.rep;
+    patch_tile<S, PREC, false, PULSE>(a, it.bx, it.by, it.bz, reinterpret_cast<float*>(smem_raw));
 }
 
 template <int S, bool PREC, bool HSITE, bool PULSE>
@@ -392,16 +423,34 @@ cudaError_t patch_dispatch(const PatchArgs& a, dim3 grid, cudaStream_t st, bool 
     return prepare ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-}  // namespace
-
-cudaError_t prepare_patch_kernels() {
-    PatchArgs a{};
-    cudaError_t e = patch_dispatch<4>(a, dim3(1), 0, false, false, false, true);
-    if (e != cudaSuccess) return e;
-    return patch_dispatch<2>(a, dim3(1), 0, false, false, false, true);
+template <int S, bool PREC, bool PULSE>
+cudaError_t batch_launch(const PatchArgs& a, const BatchItem* items, int nitems, const BatchRep* reps, cudaStream_t st,
+                         bool prepare) {
+    const size_t smem = patch_smem<S, PREC, false, PULSE>();
+    if (prepare)
+        return cudaFuncSetAttribute(k_step_patch_batch<S, PREC, PULSE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem);
+    k_step_patch_batch<S, PREC, PULSE><<<nitems, dim3(kPT, PatchShape<S>::TY), smem, st>>>(a, items, reps);
+    return cudaGetLastError();
 }
 
-cudaError_t launch_step_patch(const StepLaunch<float>& L) {
+template <int S>
+cudaError_t batch_dispatch(const PatchArgs& a, const BatchItem* items, int nitems, const BatchRep* reps,
+                           cudaStream_t st, bool prec, bool pulse, bool prepare) {
+    if (prepare) {
+        cudaError_t e;
+        if ((e = batch_launch<S, true, false>(a, items, nitems, reps, st, true)) != cudaSuccess) return e;
+        if ((e = batch_launch<S, true, true>(a, items, nitems, reps, st, true)) != cudaSuccess) return e;
+        if ((e = batch_launch<S, false, false>(a, items, nitems, reps, st, true)) != cudaSuccess) return e;
+        return batch_launch<S, false, true>(a, items, nitems, reps, st, true);
+    }
+    if (prec) return pulse ? batch_launch<S, true, true>(a, items, nitems, reps, st, false)
+                           : batch_launch<S, true, false>(a, items, nitems, reps, st, false);
+    return pulse ? batch_launch<S, false, true>(a, items, nitems, reps, st, false)
+                 : batch_launch<S, false, false>(a, items, nitems, reps, st, false);
+}
+
+PatchArgs patch_args_common(const StepLaunch<float>& L) {
     const Tableau& tb = *L.tab;
     const int S = tb.stages;
     PatchArgs a{};
@@ -432,6 +481,41 @@ cudaError_t launch_step_patch(const StepLaunch<float>& L) {
     a.replica = L.replica;
     a.sigma = L.sigma;
     a.interval = L.d_interval;
+    return a;
+}
+
+}  // namespace
+
+int patch_out_x(int stages) { return kPC - 2 * stages; }
+int patch_out_y(int stages) {
+    return (stages == 4 ? PatchShape<4>::PY * PatchShape<4>::TY : PatchShape<2>::PY * PatchShape<2>::TY) - 2 * stages;
+}
+
+cudaError_t launch_step_patch_batch(const StepLaunch<float>& L, const BatchItem* items, int nitems,
+                                    const BatchRep* reps) {
+    const PatchArgs a = patch_args_common(L);
+    const bool prec = L.precession != 0;
+    if (L.tab->stages == 4) return batch_dispatch<4>(a, items, nitems, reps, L.stream, prec, L.pulse != 0, false);
+    return batch_dispatch<2>(a, items, nitems, reps, L.stream, prec, L.pulse != 0, false);
+}
+
+cudaError_t prepare_patch_kernels() {
+    {
+        PatchArgs a{};
+        cudaError_t e = batch_dispatch<4>(a, nullptr, 0, nullptr, 0, false, false, true);
+        if (e != cudaSuccess) return e;
+        e = batch_dispatch<2>(a, nullptr, 0, nullptr, 0, false, false, true);
+        if (e != cudaSuccess) return e;
+    }
+    PatchArgs a{};
+    cudaError_t e = patch_dispatch<4>(a, dim3(1), 0, false, false, false, true);
+    if (e != cudaSuccess) return e;
+    return patch_dispatch<2>(a, dim3(1), 0, false, false, false, true);
+}
+
+cudaError_t launch_step_patch(const StepLaunch<float>& L) {
+    const int S = L.tab->stages;
+    PatchArgs a = patch_args_common(L);
     const int outx = kPC - 2 * S;
     const int outy = (S == 4 ? PatchShape<4>::PY * PatchShape<4>::TY : PatchShape<2>::PY * PatchShape<2>::TY) - 2 * S;
     const int tiles_x = (L.g.nx + outx - 1) / outx;
