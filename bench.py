@@ -227,6 +227,68 @@ def adjoint_timing(sp, torch, dev):
             "grad": {"J": g["J"], "D": g["D"], "H": g["H"]}}
 
 
+def batch_timing(sp, torch, dev, flush, stream, hbm_peak, intervals=3):
+    """Throughput of the 512-replica workload (L uniform over {16..64}, T in
+    [0.2, 2], RK4 dt=0.2, pulse every 10): whole noise intervals replayed from
+    the batch's CUDA graph, L2 flushed before each; the state (~0.5 GB) is
+    larger than L2, so the algorithmic-byte fraction is an HBM fraction."""
+    w = spin_inputs.WORKLOADS["batch512"]
+    L, T = spin_inputs.replica_draws(w["nrep"], w["seed"])
+    p = sp.Params(1, 1, 1, J=w["J"], D=w["D"], H=w["H"], lam=w["lam"], dt=w["dt"], R=w["R"], seed=w["seed"],
+                  precision=32)
+    states = [spin_inputs.random_spins(int(l), int(l), int(l), seed=1000 + r) for r, l in enumerate(L)]
+    with torch.cuda.stream(stream):
+        b = sp.Batch(p, L, T, states, device=dev, stream=stream)
+        ntot = int(b.offsets[-1])
+        for _ in range(3):
+            b.step(p.R)
+        evs = []
+        for _ in range(intervals):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b.step(p.R)
+            e1.record(stream)
+            evs.append((e0, e1))
+    torch.cuda.synchronize()
+    t = sum(a.elapsed_time(c) for a, c in evs) / 1e3
+    rate = ntot * p.R * intervals / t
+    b.close()
+    return {"workload": "512 replicas, L in {16,24,32,48,64}, T in [0.2,2], FP32 RK4 dt=0.2, pulse every 10",
+            "spins": ntot, "value": rate, "unit": "spin-steps/s", "ms_per_interval": 1e3 * t / intervals,
+            "chunk_planes": b.chunk_planes, "work_items": b.nitems,
+            "hbm_frac_algorithmic": BYTES_PER_SPIN_STEP_FP32 * rate / 1e9 / hbm_peak}
+
+
+def kernel_timing_256(sp, torch, dev, flush, stream, hbm_peak):
+    """The same fused RK4 step on a 256^3 lattice (201 MB per state copy,
+    larger than L2): plain-step launch time and its HBM fraction."""
+    w = dict(spin_inputs.WORKLOADS[WORKLOAD])
+    w["n"] = (256, 256, 256)
+    p = _params(sp, w, 0)
+    s0 = spin_inputs.random_spins(256, 256, 256, seed=w["spin_seed"])
+    with torch.cuda.stream(stream):
+        lat = sp.Lattice(p, torch.from_numpy(s0), device=dev, stream=stream)
+        lat.step(p.R)
+        ev = []
+        for _ in range(2):
+            flush.zero_()
+            torch.cuda._sleep(3_000_000)
+            for q in range(p.R):
+                a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                lat.step(1)
+                c.record(stream)
+                if (q + 1) % p.R != 0 and (q + 1) % p.R != p.R // 2:
+                    ev.append((a, c))
+    torch.cuda.synchronize()
+    ms = float(np.mean([a.elapsed_time(c) for a, c in ev]))
+    lat.close()
+    gbs = BYTES_PER_SPIN_STEP_FP32 * p.N / (ms / 1e3) / 1e9
+    return {"lattice": "256^3", "kernel_ms_per_launch": ms, "achieved_GBps": gbs, "frac": gbs / hbm_peak,
+            "spin_steps_per_s": p.N / (ms / 1e3)}
+
+
 def run_ours(args, ws, rank, local):
     import torch
 
@@ -334,6 +396,8 @@ def run_ours(args, ws, rank, local):
     d2h = host_out.numel() * host_out.element_size() + 5 * 8
 
     adj = adjoint_timing(sp, torch, dev) if rank == 0 else None
+    bat = batch_timing(sp, torch, dev, flush, stream, hbm_peak) if rank == 0 and not args.no_extra else None
+    k256 = kernel_timing_256(sp, torch, dev, flush, stream, hbm_peak) if rank == 0 and not args.no_extra else None
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -376,6 +440,8 @@ def run_ours(args, ws, rank, local):
             "gpu_launches": args.steps * (R + 2),
             "clocks": clk,
             "adjoint": adj,
+            "batched": bat,
+            "roofline_256": k256,
             "wall_s_timed_region": wall,
             "cpu_baseline": cpu,
         }
@@ -418,6 +484,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the batched and 256^3 side measurements")
     ap.add_argument("--profile-lattice", type=int, default=0,
                     help="profiling driver: L^3 FP32 RK4 lattice, --profile-steps single steps, no timing")
     ap.add_argument("--profile-steps", type=int, default=4)
