@@ -395,7 +395,7 @@ def run_ours(args, ws, rank, local):
     h2d = host_in.numel() * host_in.element_size()
     d2h = host_out.numel() * host_out.element_size() + 5 * 8
 
-    adj = adjoint_timing(sp, torch, dev) if rank == 0 else None
+    adj = adjoint_timing(sp, torch, dev) if rank == 0 and not args.no_extra else None
     bat = batch_timing(sp, torch, dev, flush, stream, hbm_peak) if rank == 0 and not args.no_extra else None
     k256 = kernel_timing_256(sp, torch, dev, flush, stream, hbm_peak) if rank == 0 and not args.no_extra else None
 
@@ -437,7 +437,7 @@ def run_ours(args, ws, rank, local):
             "roofline_alu": roof_alu,
             "e2e": {"value": e2e_value, "unit": "spin-steps/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
-            "gpu_launches": args.steps * (R + 2),
+            "gpu_launches": args.steps * (R + 3),   # R steps + pulse + 2 reduction kernels per interval
             "clocks": clk,
             "adjoint": adj,
             "batched": bat,
@@ -484,7 +484,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extra", action="store_true", help="skip the batched and 256^3 side measurements")
+    ap.add_argument("--no-extra", action="store_true", help="skip the adjoint, batched and 256^3 side measurements")
     ap.add_argument("--profile-lattice", type=int, default=0,
                     help="profiling driver: L^3 FP32 RK4 lattice, --profile-steps single steps, no timing")
     ap.add_argument("--profile-steps", type=int, default=4)

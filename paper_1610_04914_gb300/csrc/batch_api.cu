@@ -218,8 +218,15 @@ cudaError_t batch_observe(spin_batch* b, int buf, bool sample, cudaStream_t st) 
 cudaError_t batch_one_step(spin_batch* b, int from, long long n_next, cudaStream_t st) {
     const int R = b->p.steps_per_pulse;
     const bool pulse = b->p.noise && (n_next % R) == (R / 2);
-    cudaError_t e = launch_step_patch_batch(batch_launch_args(b, from, pulse, st), b->items, b->nitems, b->reps);
+    // the step kernel without its epilogue rotation, then the pulse over all
+    // sites (every thread busy; same arithmetic as the single-lattice path)
+    cudaError_t e = launch_step_patch_batch(batch_launch_args(b, from, false, st), b->items, b->nitems, b->reps);
     if (e != cudaSuccess) return e;
+    if (pulse) {
+        float* s[3] = {(float*)b->buf[from ^ 1][0], (float*)b->buf[from ^ 1][1], (float*)b->buf[from ^ 1][2]};
+        e = launch_pulse_batch(s, b->reps, b->oblocks, b->nblocks_obs, b->p.seed, b->d_interval, st);
+        if (e != cudaSuccess) return e;
+    }
     if (n_next % R == 0) e = batch_observe(b, from ^ 1, true, st);
     return e;
 }

@@ -86,6 +86,9 @@ struct ObsBlock {
     int row0;
     int nrows;
 };
+// Pulse rotation of every site of every replica (block table as above).
+cudaError_t launch_pulse_batch(float* s[3], const BatchRep* reps, const ObsBlock* blocks, int nblocks, uint64_t seed,
+                               const long long* d_interval, cudaStream_t st);
 cudaError_t launch_observables_batch(const float* s[3], const BatchRep* reps, const ObsBlock* blocks, int nblocks,
                                      const int* first_block, int nrep, Phys<double> ph, double* partials,
                                      double* out, double* ring, int ring_len, long long* d_interval,

@@ -101,6 +101,8 @@ struct PThread {
     int col[PY][2];    // [row][pair element] global column index gy*nx+gx
     bool out[PY][2];
     int plane;         // nx*ny
+    int gz_issue;      // wrapped z of the next plane to prefetch (t+S+2)
+    int gz_field;      // wrapped z of the next site-field plane (t+S-1)
 };
 
 // Per-thread staging ring for spin planes fetched two iterations ahead with
@@ -131,7 +133,7 @@ __device__ __forceinline__ void issue_plane(const PatchArgs& a, float* stg, cons
 
 template <int S, bool PREC, bool HSITE, bool PULSE, int P>
 __device__ __forceinline__ void patch_iteration(const PatchArgs& a, PRings<S, HSITE>& r, float* __restrict__ sh,
-                                                float* __restrict__ stg, const PThread<PatchShape<S>::PY>& th, int i,
+                                                float* __restrict__ stg, PThread<PatchShape<S>::PY>& th, int i,
                                                 int t0, int z0, long long k, int tid) {
     constexpr int PY = PatchShape<S>::PY, ROWS = PatchShape<S>::PY * PatchShape<S>::TY;
     constexpr int TILE = ROWS * kRS;
@@ -156,7 +158,8 @@ __device__ __forceinline__ void patch_iteration(const PatchArgs& a, PRings<S, HS
     //    ago); plane t+S+2 is requested now
     const int t = i + t0;
     {
-        issue_plane<S>(a, stg, th, (P + S + 2) & 3, wrapi(t + S + 2, a.nz), tid);
+        issue_plane<S>(a, stg, th, (P + S + 2) & 3, th.gz_issue, tid);
+        th.gz_issue = th.gz_issue + 1 == a.nz ? 0 : th.gz_issue + 1;
         cp_async_wait<2>();
         const int slot = (P + S) & 3;
 #pragma unroll
@@ -166,7 +169,8 @@ __device__ __forceinline__ void patch_iteration(const PatchArgs& a, PRings<S, HS
                 r.s[slot][rr][c] = make_float2(*stage_slot<S>(stg, slot, c, rr, 0, tid),
                                                *stage_slot<S>(stg, slot, c, rr, 1, tid));
         if (HSITE) {
-            const long long bh = (long long)wrapi(t + S - 1, a.nz) * th.plane;
+            const long long bh = (long long)th.gz_field * th.plane;
+            th.gz_field = th.gz_field + 1 == a.nz ? 0 : th.gz_field + 1;
             const int sl = (P + S - 1) & 3;
 #pragma unroll
             for (int rr = 0; rr < PY; ++rr) {
@@ -340,6 +344,8 @@ __device__ __forceinline__ void patch_tile(const PatchArgs& a, int bx, int by, i
     // planes S and S+1 (local) go to the staging ring before the march
     issue_plane<S>(a, stg, th, S & 3, wrapi(t0 + S, a.nz), tid);
     issue_plane<S>(a, stg, th, (S + 1) & 3, wrapi(t0 + S + 1, a.nz), tid);
+    th.gz_issue = wrapi(t0 + S + 2, a.nz);
+    th.gz_field = wrapi(t0 + S - 1, a.nz);
     int i = 0;
     for (; i + 4 <= a.n_iter; i += 4) {
         patch_iteration<S, PREC, HSITE, PULSE, 0>(a, r, sh, stg, th, i + 0, t0, z0, k, tid);
@@ -484,7 +490,53 @@ PatchArgs patch_args_common(const StepLaunch<float>& L) {
     return a;
 }
 
+// The noise pulse on its own, over every site of the lattice (all threads
+// busy): on pulse steps of a single lattice the step kernel runs without its
+// epilogue rotation and this kernel rotates the finished state in place.  The
+// arithmetic per site is the fused epilogue's, so the results are identical.
+__global__ void __launch_bounds__(256) k_pulse_f32(float* __restrict__ sx, float* __restrict__ sy, float* __restrict__ sz,
+                                                   long long N, uint64_t seed, const long long* __restrict__ interval,
+                                                   uint64_t replica, float sigma) {
+    const uint64_t k = (uint64_t)*interval;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        float x = sx[i], y = sy[i], z = sz[i];
+        pulse_site<float>(x, y, z, seed, (uint64_t)i, k, replica, sigma);
+        sx[i] = x;
+        sy[i] = y;
+        sz[i] = z;
+    }
+}
+
+// Batched pulse: block b rotates the sites of rows [row0, row0+nrows) of
+// replica rep (the observables' block table), with that replica's angle scale
+// and noise stream; same per-site arithmetic as the single-lattice kernel.
+__global__ void __launch_bounds__(256) k_pulse_batch(float* __restrict__ sx, float* __restrict__ sy,
+                                                     float* __restrict__ sz, const BatchRep* __restrict__ reps,
+                                                     const ObsBlock* __restrict__ blocks, uint64_t seed,
+                                                     const long long* __restrict__ interval) {
+    const ObsBlock ob = blocks[blockIdx.x];
+    const BatchRep rp = reps[ob.rep];
+    const uint64_t k = (uint64_t)*interval;
+    const long long first = (long long)ob.row0 * rp.L;
+    const long long count = (long long)ob.nrows * rp.L;
+    for (long long q = threadIdx.x; q < count; q += blockDim.x) {
+        const long long i = first + q;          // site index within the replica
+        const long long g = rp.off + i;
+        float x = sx[g], y = sy[g], z = sz[g];
+        pulse_site<float>(x, y, z, seed, (uint64_t)i, k, (uint64_t)ob.rep, rp.sigma);
+        sx[g] = x;
+        sy[g] = y;
+        sz[g] = z;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_pulse_batch(float* s[3], const BatchRep* reps, const ObsBlock* blocks, int nblocks, uint64_t seed,
+                               const long long* d_interval, cudaStream_t st) {
+    k_pulse_batch<<<nblocks, 256, 0, st>>>(s[0], s[1], s[2], reps, blocks, seed, d_interval);
+    return cudaGetLastError();
+}
 
 int patch_out_x(int stages) { return kPC - 2 * stages; }
 int patch_out_y(int stages) {
@@ -542,8 +594,14 @@ cudaError_t launch_step_patch(const StepLaunch<float>& L) {
     dim3 grid(tiles_x, tiles_y, (L.g.nz + zc - 1) / zc);
     const bool hs = L.hs[0] != nullptr;
     const bool prec = L.precession != 0;
-    if (S == 4) return patch_dispatch<4>(a, grid, L.stream, prec, hs, L.pulse != 0, false);
-    return patch_dispatch<2>(a, grid, L.stream, prec, hs, L.pulse != 0, false);
+    cudaError_t e = S == 4 ? patch_dispatch<4>(a, grid, L.stream, prec, hs, false, false)
+                           : patch_dispatch<2>(a, grid, L.stream, prec, hs, false, false);
+    if (e != cudaSuccess || !L.pulse) return e;
+    const long long N = L.g.N();
+    const int blocks = (int)std::max<long long>(1, std::min<long long>((N + 255) / 256, 152LL * 8));
+    k_pulse_f32<<<blocks, 256, 0, L.stream>>>(L.out[0], L.out[1], L.out[2], N, L.seed, L.d_interval, L.replica,
+                                              L.sigma);
+    return cudaGetLastError();
 }
 
 }  // namespace spin
