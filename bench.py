@@ -289,6 +289,33 @@ def kernel_timing_256(sp, torch, dev, flush, stream, hbm_peak):
             "spin_steps_per_s": p.N / (ms / 1e3)}
 
 
+def fp64_step_timing(sp, torch, dev, flush, stream):
+    """The plain FP64 GPU step on the same 128^3 workload (the comparison arm
+    for the FP32 path's accuracy/speed trade): plain-step launch time."""
+    w = spin_inputs.WORKLOADS[WORKLOAD]
+    p = _params(sp, w, 0)
+    import dataclasses
+    p = dataclasses.replace(p, precision=64)
+    s0 = spin_inputs.random_spins(p.nx, p.ny, p.nz, seed=w["spin_seed"])
+    with torch.cuda.stream(stream):
+        lat = sp.Lattice(p, torch.from_numpy(s0), device=dev, stream=stream)
+        lat.step(1)
+        flush.zero_()
+        torch.cuda._sleep(3_000_000)
+        ev = []
+        for q in range(3):
+            a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            lat.step(1)
+            c.record(stream)
+            ev.append((a, c))
+    torch.cuda.synchronize()
+    ms = float(np.mean([a.elapsed_time(c) for a, c in ev]))
+    lat.close()
+    return {"lattice": "128^3 FP64 RK4 (fused FP64 kernel)", "kernel_ms_per_launch": ms,
+            "spin_steps_per_s": p.N / (ms / 1e3)}
+
+
 def run_ours(args, ws, rank, local):
     import torch
 
@@ -398,6 +425,7 @@ def run_ours(args, ws, rank, local):
     adj = adjoint_timing(sp, torch, dev) if rank == 0 and not args.no_extra else None
     bat = batch_timing(sp, torch, dev, flush, stream, hbm_peak) if rank == 0 and not args.no_extra else None
     k256 = kernel_timing_256(sp, torch, dev, flush, stream, hbm_peak) if rank == 0 and not args.no_extra else None
+    f64 = fp64_step_timing(sp, torch, dev, flush, stream) if rank == 0 and not args.no_extra else None
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -442,6 +470,7 @@ def run_ours(args, ws, rank, local):
             "adjoint": adj,
             "batched": bat,
             "roofline_256": k256,
+            "fp64_step": f64,
             "wall_s_timed_region": wall,
             "cpu_baseline": cpu,
         }

@@ -215,8 +215,9 @@ __device__ __forceinline__ void patch_iteration(const PatchArgs& a, PRings<S, HS
                     const f2 other = (j == 1) ? r.s[slot][ro][c] : r.x[j - 2][slot][ro][c];
                     const f2 ym = rr == 0 ? row_up : other;
                     const f2 yp = rr == PY - 1 ? row_dn : other;
-                    // neighbour order x-1, x+1, y-1, y+1, z-1, z+1
-                    sum[rr][c] = add2(add2(add2(add2(add2(xm, xp), ym), yp), ZM), ZP);
+                    // ((x-1 + x+1) + (y-1 + y+1)) + z-1, and z+1 last: it is the
+                    // value the previous stage produced in this iteration
+                    sum[rr][c] = add2(add2(add2(add2(xm, xp), add2(ym, yp)), ZM), ZP);
                     cen[rr][c] = C;
                 }
             }
