@@ -20,6 +20,8 @@ NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr"]
+# extra nvcc flags (e.g. -D tile-shape overrides for tuning experiments)
+FLAGS += os.environ.get("SPIN_NVCC_FLAGS", "").split()
 
 
 def _sources():

@@ -36,9 +36,12 @@ constexpr int kRS = kPC;       // shared row stride (floats)
 // per thread (register rings of 4 stage planes do not fit twice), RK2/Heun two.
 template <int S>
 struct PatchShape;
+#ifndef SPIN_PATCH_TY4
+#define SPIN_PATCH_TY4 24
+#endif
 template <>
 struct PatchShape<4> {
-    static constexpr int PY = 1, TY = 24;
+    static constexpr int PY = 1, TY = SPIN_PATCH_TY4;
 };
 template <>
 struct PatchShape<2> {
