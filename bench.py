@@ -49,6 +49,25 @@ def _dist():
     return ws, rank, local
 
 
+def whole_job_rate(t_local_s: float, units_local: float):
+    """Whole-job throughput of independent replicas, one per rank: units summed
+    over ranks divided by the slowest rank's timed duration.  Returns
+    (value, t_max, units_total); single process when torch.distributed is
+    not initialised."""
+    import torch
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+        t = torch.tensor([t_local_s], dtype=torch.float64, device=dev)
+        u = torch.tensor([units_local], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        t_max, units = float(t.item()), float(u.item())
+    else:
+        t_max, units = float(t_local_s), float(units_local)
+    return units / t_max, t_max, units
+
+
 def _measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -367,12 +386,7 @@ def run_ours(args, ws, rank, local):
     wall = time.perf_counter() - wall0
     step_ms = [a.elapsed_time(bb) for a, bb in ev]
     clk = clocks.stop()
-    t_dev = sum(step_ms) / 1e3
-    if ws > 1:
-        tt = torch.tensor([t_dev], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_dev = float(tt.item())
-    value = ws * N * R * args.steps / t_dev
+    value, t_dev, _ = whole_job_rate(sum(step_ms) / 1e3, N * R * args.steps)
 
     # dominant kernel: the fused RK4 step, timed launch by launch with events
     # on the launching stream.  A sleep kernel first lets the host queue the
@@ -418,7 +432,7 @@ def run_ours(args, ws, rank, local):
             smp = lat.samples()          # synchronises the stream; reads the sample record
             stream.synchronize()
             e2e_t.append(time.perf_counter() - t0)
-    e2e_value = ws * N * R * args.steps / sum(e2e_t)
+    e2e_value, _, _ = whole_job_rate(sum(e2e_t), N * R * args.steps)
     h2d = host_in.numel() * host_in.element_size()
     d2h = host_out.numel() * host_out.element_size() + 5 * 8
 
