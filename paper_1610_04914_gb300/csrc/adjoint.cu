@@ -33,10 +33,11 @@ __device__ __forceinline__ int wrapa(int v, int n) {
 }
 
 __device__ __forceinline__ void site_xyz(long long i, int nx, int ny, int& x, int& y, int& z) {
-    x = (int)(i % nx);
-    const long long r = i / nx;
-    y = (int)(r % ny);
-    z = (int)(r / ny);
+    const int ii = (int)i;   // N < 2^31
+    x = ii % nx;
+    const int r = ii / nx;
+    y = r % ny;
+    z = r / ny;
 }
 
 __device__ __forceinline__ void neighbours(long long i, int nx, int ny, int nz, long long nb[6]) {
@@ -230,10 +231,12 @@ __global__ void __launch_bounds__(kAT) k_adj_w(const real* __restrict__ x, const
         pH1 += (double)wi[1];
         pH2 += (double)wi[2];
     }
+    // each block adds into its own FP64 record, launch after launch in stream
+    // order (deterministic); the records are summed once after the backward pass
     const double vals[5] = {pJ, pD, pH0, pH1, pH2};
     for (int q = 0; q < 5; ++q) {
         const double t = block_sum<double>(vals[q], red);
-        if (threadIdx.x == 0) partials[(long long)blockIdx.x * 5 + q] = t;
+        if (threadIdx.x == 0) partials[(long long)blockIdx.x * 5 + q] += t;
     }
 }
 
@@ -427,6 +430,9 @@ cudaError_t adjoint_run(const AdjointRun<real>& A) {
                                                     H2, A.dLdE, A.dLdM[0], A.dLdM[1], A.dLdM[2]);
     k_adj_seed_finish<<<1, kAT, 0, st>>>(partials, nb, acc, A.dLdE, (double)N);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // per-block FP64 records of the stage transposes start at zero
+    e = cudaMemsetAsync(partials, 0, sizeof(double) * 5 * (size_t)nb, st);
+    if (e != cudaSuccess) return e;
 
     const long long total = A.n_end - A.n0;
     const int nseg = (int)((total + A.K - 1) / A.K);
@@ -510,7 +516,6 @@ cudaError_t adjoint_run(const AdjointRun<real>& A) {
                     if (HS) k_adj_w<real, false, true><<<nb, kAT, 0, st>>>(X[j], hs, LK[j], w, u, A.g_h, partials, g.nx, g.ny, g.nz, J, twoD, H0, H1, H2, lamb, dt);
                     else k_adj_w<real, false, false><<<nb, kAT, 0, st>>>(X[j], nullptr, LK[j], w, u, A.g_h, partials, g.nx, g.ny, g.nz, J, twoD, H0, H1, H2, lamb, dt);
                 }
-                k_adj_accumulate<<<1, kAT, 0, st>>>(partials, nb, acc, 1.0);
                 XArgs<real> xa{};
                 xa.w = w;
                 xa.u = u;
@@ -527,6 +532,8 @@ cudaError_t adjoint_run(const AdjointRun<real>& A) {
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
     }
+    k_adj_accumulate<<<1, kAT, 0, st>>>(partials, nb, acc, 1.0);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // results: gradient accumulators to the host, dL/ds_0 to the caller
     if (A.g_s0) {
         e = cudaMemcpyAsync(A.g_s0, lam, compb, cudaMemcpyDeviceToDevice, st);
