@@ -137,7 +137,7 @@ class ClockSampler:
 
 def _kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("spin_device.cuh", "step_kernels.cu"):
+    for f in ("spin_device.cuh", "step_kernels.cu", "step_patch.cu"):
         h.update(open(os.path.join(ROOT, "paper_1610_04914_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
