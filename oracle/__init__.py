@@ -46,6 +46,7 @@ class _Params(ctypes.Structure):
         ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
         ("integrator", ctypes.c_int32), ("precession", ctypes.c_int32),
         ("R", ctypes.c_int32), ("renorm", ctypes.c_int32), ("replica", ctypes.c_int32),
+        ("bc", ctypes.c_int32), ("unused", ctypes.c_int32),
         ("J", ctypes.c_double), ("D", ctypes.c_double), ("H", ctypes.c_double * 3),
         ("lambda_", ctypes.c_double), ("T", ctypes.c_double), ("dt", ctypes.c_double),
         ("seed", ctypes.c_uint64),
@@ -70,6 +71,7 @@ class Params:
     renorm: int = 1
     seed: int = 1
     replica: int = 0
+    bc: int = 0                    # 0: periodic, 1: free
 
     @property
     def N(self) -> int:
@@ -77,7 +79,7 @@ class Params:
 
     def c(self) -> _Params:
         return _Params(self.nx, self.ny, self.nz, self.integrator, self.precession,
-                       self.R, self.renorm, self.replica, self.J, self.D,
+                       self.R, self.renorm, self.replica, self.bc, 0, self.J, self.D,
                        (ctypes.c_double * 3)(*self.H), self.lam, self.T, self.dt,
                        self.seed & 0xFFFFFFFFFFFFFFFF)
 

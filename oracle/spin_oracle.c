@@ -14,8 +14,8 @@
  *
  * Units: gamma = mu0 = k_B = 1 (paper, end of Sec. II).
  *
- * Lattice: simple cubic nx*ny*nz, periodic boundaries, site index
- * i = x + nx*(y + ny*z).  Spin state is structure-of-arrays:
+ * Lattice: simple cubic nx*ny*nz, periodic or free boundaries (the paper's
+ * particle of Sec. IV has free ones), site index i = x + nx*(y + ny*z).  Spin state is structure-of-arrays:
  * s[0*N+i] = s_x, s[1*N+i] = s_y, s[2*N+i] = s_z.
  *
  * Parity status of each function (what pins it) is listed beside it.
@@ -38,6 +38,8 @@ typedef struct {
     int32_t R;               /* steps per noise interval, R = Delta t / delta t >= 1 */
     int32_t renorm;          /* 1: s <- s/|s| after every full step */
     int32_t replica;         /* third Philox counter word */
+    int32_t bc;              /* 0: periodic; 1: free (missing neighbours contribute nothing) */
+    int32_t unused;
     double J, D, H[3];       /* exchange, uniaxial anisotropy (z), Zeeman field */
     double lambda, T, dt;    /* damping, temperature, integration step delta t */
     uint64_t seed;           /* Philox key word 0 for the noise pulses */
@@ -118,8 +120,11 @@ void orc_noise_gauss(uint64_t seed, int64_t site, int64_t k, int64_t replica, do
 /* uniform-state single-spin map, and the Metropolis equilibrium.           */
 /* ------------------------------------------------------------------------ */
 
+/* Index of site (x, y, z); with free boundaries a position outside the
+   lattice has no site and gives -1. */
 static int64_t site_index(const orc_params *p, int x, int y, int z)
 {
+    if (p->bc == 1 && (x < 0 || x >= p->nx || y < 0 || y >= p->ny || z < 0 || z >= p->nz)) return -1;
     x = (x % p->nx + p->nx) % p->nx;
     y = (y % p->ny + p->ny) % p->ny;
     z = (z % p->nz + p->nz) % p->nz;
@@ -138,7 +143,8 @@ static void heff_site(const orc_params *p, const double *s, const double *hsite,
     const int64_t i = site_index(p, x, y, z);
     for (int a = 0; a < 3; ++a) {
         double sum = 0.0;
-        for (int j = 0; j < 6; ++j) sum += s[a * N + nb[j]];
+        for (int j = 0; j < 6; ++j)
+            if (nb[j] >= 0) sum += s[a * N + nb[j]];
         Heff[a] = p->J * sum + p->H[a];
         if (hsite) Heff[a] += hsite[a * N + i];
     }
@@ -344,6 +350,7 @@ void orc_observables(const orc_params *p, const double *s, const double *hsite, 
                 for (int a = 0; a < 3; ++a) M[a] += si[a];
                 for (int b = 0; b < 3; ++b) {
                     int64_t j = fwd[b];
+                    if (j < 0) continue;
                     E -= p->J * (si[0] * s[j] + si[1] * s[N + j] + si[2] * s[2 * N + j]);
                 }
                 E -= p->D * si[2] * si[2];
@@ -441,7 +448,7 @@ int64_t orc_metropolis(const orc_params *p, double *s, const double *hsite,
                         for (int j = 0; j < 6; ++j) {
                             /* a site that neighbours itself (lattice size 1)
                                moves together with the trial spin */
-                            if (nb[j] == i) continue;
+                            if (nb[j] == i || nb[j] < 0) continue;
                             sum += s[a * N + nb[j]];
                         }
                         loc[a] = p->J * sum + p->H[a] + (hsite ? hsite[a * N + i] : 0.0);
@@ -546,7 +553,8 @@ void orc_rhs_vjp(const orc_params *p, const double *x, const double *hsite, cons
                 };
                 for (int c = 0; c < 3; ++c) {
                     double sum = 0.0;
-                    for (int j = 0; j < 6; ++j) sum += x[c * N + nb[j]];
+                    for (int j = 0; j < 6; ++j)
+                        if (nb[j] >= 0) sum += x[c * N + nb[j]];
                     if (gJ) *gJ += wi[c] * sum;
                     if (gH) gH[c] += wi[c];
                     if (gh) gh[c * N + i] += wi[c];
@@ -564,7 +572,8 @@ void orc_rhs_vjp(const orc_params *p, const double *x, const double *hsite, cons
                 };
                 for (int c = 0; c < 3; ++c) {
                     double sum = 0.0;
-                    for (int j = 0; j < 6; ++j) sum += w[c * N + nb[j]];
+                    for (int j = 0; j < 6; ++j)
+                        if (nb[j] >= 0) sum += w[c * N + nb[j]];
                     out[c * N + i] += p->J * sum;
                 }
                 out[2 * N + i] += 2.0 * p->D * w[2 * N + i];
@@ -672,7 +681,8 @@ void orc_adjoint(const orc_params *p, const double *s0, const double *hsite, int
                 int64_t fwd[3] = {site_index(p, x + 1, y, z), site_index(p, x, y + 1, z),
                                   site_index(p, x, y, z + 1)};
                 for (int b = 0; b < 3; ++b)
-                    for (int c = 0; c < 3; ++c) bonds += fin[c * N + i] * fin[c * N + fwd[b]];
+                    if (fwd[b] >= 0)
+                        for (int c = 0; c < 3; ++c) bonds += fin[c * N + i] * fin[c * N + fwd[b]];
                 sz2 += fin[2 * N + i] * fin[2 * N + i];
                 for (int c = 0; c < 3; ++c) {
                     M[c] += fin[c * N + i];
