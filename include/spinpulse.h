@@ -60,7 +60,7 @@ typedef enum spin_integrator {
 
 /* Problem statement of one lattice (paper Sec. II and IV). */
 typedef struct spin_params {
-    int32_t nx, ny, nz;       /* lattice size, each >= 1; periodic boundaries */
+    int32_t nx, ny, nz;       /* lattice size, each >= 1 */
     int32_t precision;        /* 32 (float state) or 64 (double state) */
     int32_t integrator;       /* spin_integrator */
     int32_t precession;       /* 1: full Eq. (LLL); 0: slow equation, precession dropped (Sec. II) */
@@ -71,7 +71,10 @@ typedef struct spin_params {
     int32_t path;             /* 0: fused single-kernel step where the tableau allows
                                  (RK4, RK2 midpoint, Heun), else per-stage kernels;
                                  1: per-stage kernels always (cross-check path) */
-    int32_t reserved;         /* must be 0 */
+    int32_t bc;               /* 0: periodic boundaries; 1: free boundaries (the paper's
+                                 particle, Sec. IV): a site on a face has no neighbour
+                                 across it; batch replicas and the no-alloc observables
+                                 are periodic only */
     double J;                 /* nearest-neighbour exchange; E = -J sum_<ij> s_i.s_j */
     double D;                 /* uniaxial anisotropy along z; E = -D sum s_z^2 */
     double H[3];              /* uniform Zeeman field; E = -sum H.s */

@@ -40,7 +40,7 @@ class spin_params(ctypes.Structure):
         ("precision", ctypes.c_int32), ("integrator", ctypes.c_int32),
         ("precession", ctypes.c_int32), ("steps_per_pulse", ctypes.c_int32),
         ("renorm", ctypes.c_int32), ("noise", ctypes.c_int32), ("replica", ctypes.c_int32),
-        ("path", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("path", ctypes.c_int32), ("bc", ctypes.c_int32),
         ("J", ctypes.c_double), ("D", ctypes.c_double), ("H", ctypes.c_double * 3),
         ("lambda_", ctypes.c_double), ("T", ctypes.c_double), ("dt", ctypes.c_double),
         ("seed", ctypes.c_uint64),

@@ -40,6 +40,23 @@ __device__ __forceinline__ void site_xyz(long long i, int nx, int ny, int& x, in
     z = r / ny;
 }
 
+// Neighbour indices x-1, x+1, y-1, y+1, z-1, z+1 (periodic), and in w the
+// weight of each: 0 for a neighbour across a face of a free-boundary lattice.
+template <typename real>
+__device__ __forceinline__ void neighbour_weights(long long i, int nx, int ny, int nz, int bc, real w[6]) {
+    int x, y, z;
+    const int ii = (int)i;
+    x = ii % nx;
+    y = (ii / nx) % ny;
+    z = (ii / nx) / ny;
+    w[0] = (bc && x == 0) ? real(0) : real(1);
+    w[1] = (bc && x == nx - 1) ? real(0) : real(1);
+    w[2] = (bc && y == 0) ? real(0) : real(1);
+    w[3] = (bc && y == ny - 1) ? real(0) : real(1);
+    w[4] = (bc && z == 0) ? real(0) : real(1);
+    w[5] = (bc && z == nz - 1) ? real(0) : real(1);
+}
+
 __device__ __forceinline__ void neighbours(long long i, int nx, int ny, int nz, long long nb[6]) {
     int x, y, z;
     site_xyz(i, nx, ny, x, y, z);
@@ -83,12 +100,13 @@ __device__ __forceinline__ T block_sum(T v, T* red) {
 // evaluated in the storage precision like the forward kernels).
 template <typename real, bool HSITE>
 __device__ __forceinline__ void heff_at(const real* __restrict__ x, const real* __restrict__ hs, long long i,
-                                        const long long nb[6], long long N, real J, real twoD, const real H[3],
-                                        real h[3]) {
+                                        const long long nb[6], const real wn[6], long long N, real J, real twoD,
+                                        const real H[3], real h[3]) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const real* q = x + c * N;
-        const real sum = q[nb[0]] + q[nb[1]] + q[nb[2]] + q[nb[3]] + q[nb[4]] + q[nb[5]];
+        const real sum = wn[0] * q[nb[0]] + wn[1] * q[nb[1]] + wn[2] * q[nb[2]] + wn[3] * q[nb[3]] + wn[4] * q[nb[4]] +
+                         wn[5] * q[nb[5]];
         h[c] = J * sum + H[c];
         if (HSITE) h[c] += hs[c * N + i];
     }
@@ -98,14 +116,16 @@ __device__ __forceinline__ void heff_at(const real* __restrict__ x, const real* 
 // K = dt f(x) over component-major arrays.
 template <typename real, bool PREC, bool HSITE>
 __global__ void k_adj_rhs(const real* __restrict__ x, const real* __restrict__ hs, real* __restrict__ K, int nx, int ny,
-                          int nz, real J, real twoD, real H0, real H1, real H2, real lambda, real dt) {
+                          int nz, real J, real twoD, real H0, real H1, real H2, real lambda, real dt, int bc) {
     const long long N = (long long)nx * ny * nz;
     const real H[3] = {H0, H1, H2};
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
         long long nb[6];
         neighbours(i, nx, ny, nz, nb);
+        real wn[6];
+        neighbour_weights<real>(i, nx, ny, nz, bc, wn);
         real h[3];
-        heff_at<real, HSITE>(x, hs, i, nb, N, J, twoD, H, h);
+        heff_at<real, HSITE>(x, hs, i, nb, wn, N, J, twoD, H, h);
         real f[3];
         llg_rhs<real, PREC>(x[i], x[N + i], x[2 * N + i], h[0], h[1], h[2], lambda, f[0], f[1], f[2]);
         K[i] = dt * f[0];
@@ -184,7 +204,7 @@ __global__ void __launch_bounds__(kAT) k_adj_w(const real* __restrict__ x, const
                                                const real* __restrict__ LK, real* __restrict__ w, real* __restrict__ u,
                                                double* __restrict__ gh, double* __restrict__ partials, int nx, int ny,
                                                int nz, real J, real twoD, real H0, real H1, real H2, real lambda,
-                                               real dt) {
+                                               real dt, int bc) {
     __shared__ double red[kAT / 32];
     const long long N = (long long)nx * ny * nz;
     const real H[3] = {H0, H1, H2};
@@ -192,8 +212,10 @@ __global__ void __launch_bounds__(kAT) k_adj_w(const real* __restrict__ x, const
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
         long long nb[6];
         neighbours(i, nx, ny, nz, nb);
+        real wn[6];
+        neighbour_weights<real>(i, nx, ny, nz, bc, wn);
         real hr[3];
-        heff_at<real, HSITE>(x, hs, i, nb, N, J, twoD, H, hr);
+        heff_at<real, HSITE>(x, hs, i, nb, wn, N, J, twoD, H, hr);
         // the transpose in the state precision (like the forward stages);
         // the parameter gradients accumulate in FP64
         const real s[3] = {x[i], x[N + i], x[2 * N + i]};
@@ -223,7 +245,8 @@ __global__ void __launch_bounds__(kAT) k_adj_w(const real* __restrict__ x, const
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const real* q = x + c * N;
-            sn[c] = q[nb[0]] + q[nb[1]] + q[nb[2]] + q[nb[3]] + q[nb[4]] + q[nb[5]];
+            sn[c] = wn[0] * q[nb[0]] + wn[1] * q[nb[1]] + wn[2] * q[nb[2]] + wn[3] * q[nb[3]] + wn[4] * q[nb[4]] +
+                    wn[5] * q[nb[5]];
         }
         pJ += (double)(wi[0] * sn[0] + wi[1] * sn[1] + wi[2] * sn[2]);
         pD += (double)(real(2) * s[2] * wi[2]);
@@ -251,6 +274,7 @@ struct XArgs {
     real a[6];
     int nl;
     real J, twoD;
+    int bc;
 };
 
 template <typename real>
@@ -259,10 +283,13 @@ __global__ void k_adj_x(XArgs<real> a, int nx, int ny, int nz) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
         long long nb[6];
         neighbours(i, nx, ny, nz, nb);
+        real wn[6];
+        neighbour_weights<real>(i, nx, ny, nz, a.bc, wn);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const real* q = a.w + c * N;
-            real lx = a.u[c * N + i] + a.J * (q[nb[0]] + q[nb[1]] + q[nb[2]] + q[nb[3]] + q[nb[4]] + q[nb[5]]);
+            real lx = a.u[c * N + i] + a.J * (wn[0] * q[nb[0]] + wn[1] * q[nb[1]] + wn[2] * q[nb[2]] + wn[3] * q[nb[3]] +
+                                              wn[4] * q[nb[4]] + wn[5] * q[nb[5]]);
             if (c == 2) lx += a.twoD * a.w[2 * N + i];
             a.lam[c * N + i] += lx;
             for (int l = 0; l < a.nl; ++l)
@@ -289,7 +316,7 @@ __global__ void __launch_bounds__(kAT) k_adj_seed(const real* __restrict__ s, co
                                                   real* __restrict__ lam, double* __restrict__ gh,
                                                   double* __restrict__ partials, int nx, int ny, int nz, real J,
                                                   real twoD, real H0, real H1, real H2, double dLdE, double dM0,
-                                                  double dM1, double dM2) {
+                                                  double dM1, double dM2, int bc) {
     __shared__ double red[kAT / 32];
     const long long N = (long long)nx * ny * nz;
     const real H[3] = {H0, H1, H2};
@@ -298,17 +325,20 @@ __global__ void __launch_bounds__(kAT) k_adj_seed(const real* __restrict__ s, co
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
         long long nb[6];
         neighbours(i, nx, ny, nz, nb);
+        real wn[6];
+        neighbour_weights<real>(i, nx, ny, nz, bc, wn);
         real h[3];
-        heff_at<real, HSITE>(s, hs, i, nb, N, J, twoD, H, h);
+        heff_at<real, HSITE>(s, hs, i, nb, wn, N, J, twoD, H, h);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             lam[c * N + i] = (real)((-dLdE * (double)h[c] + dM[c]) / (double)N);
             if (gh) gh[c * N + i] += -dLdE * (double)s[c * N + i] / (double)N;
         }
         const double a = s[i], b = s[N + i], c = s[2 * N + i];
-        bonds += a * ((double)s[nb[1]] + (double)s[nb[3]] + (double)s[nb[5]]) +
-                 b * ((double)s[N + nb[1]] + (double)s[N + nb[3]] + (double)s[N + nb[5]]) +
-                 c * ((double)s[2 * N + nb[1]] + (double)s[2 * N + nb[3]] + (double)s[2 * N + nb[5]]);
+        const double w1 = wn[1], w3 = wn[3], w5 = wn[5];   // forward bonds inside the lattice
+        bonds += a * (w1 * s[nb[1]] + w3 * s[nb[3]] + w5 * s[nb[5]]) +
+                 b * (w1 * s[N + nb[1]] + w3 * s[N + nb[3]] + w5 * s[N + nb[5]]) +
+                 c * (w1 * s[2 * N + nb[1]] + w3 * s[2 * N + nb[3]] + w5 * s[2 * N + nb[5]]);
         sz2 += c * c;
         m0 += a;
         m1 += b;
@@ -424,10 +454,10 @@ cudaError_t adjoint_run(const AdjointRun<real>& A) {
     k_gather3<real><<<grid_for(N), kAT, 0, st>>>(fin, A.final_state[0], A.final_state[1], A.final_state[2], N);
     if (HS)
         k_adj_seed<real, true><<<nb, kAT, 0, st>>>(fin, hs, lam, A.g_h, partials, g.nx, g.ny, g.nz, J, twoD, H0, H1, H2,
-                                                   A.dLdE, A.dLdM[0], A.dLdM[1], A.dLdM[2]);
+                                                   A.dLdE, A.dLdM[0], A.dLdM[1], A.dLdM[2], A.bc);
     else
         k_adj_seed<real, false><<<nb, kAT, 0, st>>>(fin, nullptr, lam, A.g_h, partials, g.nx, g.ny, g.nz, J, twoD, H0, H1,
-                                                    H2, A.dLdE, A.dLdM[0], A.dLdM[1], A.dLdM[2]);
+                                                    H2, A.dLdE, A.dLdM[0], A.dLdM[1], A.dLdM[2], A.bc);
     k_adj_seed_finish<<<1, kAT, 0, st>>>(partials, nb, acc, A.dLdE, (double)N);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // per-block FP64 records of the stage transposes start at zero
@@ -477,11 +507,11 @@ cudaError_t adjoint_run(const AdjointRun<real>& A) {
                 lc.nk = j;
                 k_adj_lincomb<real><<<grid_for(len), kAT, 0, st>>>(X[j], s, lc, len);
                 if (A.precession) {
-                    if (HS) k_adj_rhs<real, true, true><<<grid_for(N), kAT, 0, st>>>(X[j], hs, Kst[j], g.nx, g.ny, g.nz, J, twoD, H0, H1, H2, lamb, dt);
-                    else k_adj_rhs<real, true, false><<<grid_for(N), kAT, 0, st>>>(X[j], nullptr, Kst[j], g.nx, g.ny, g.nz, J, twoD, H0, H1, H2, lamb, dt);
+                    if (HS) k_adj_rhs<real, true, true><<<grid_for(N), kAT, 0, st>>>(X[j], hs, Kst[j], g.nx, g.ny, g.nz, J, twoD, H0, H1, H2, lamb, dt, A.bc);
+                    else k_adj_rhs<real, true, false><<<grid_for(N), kAT, 0, st>>>(X[j], nullptr, Kst[j], g.nx, g.ny, g.nz, J, twoD, H0, H1, H2, lamb, dt, A.bc);
                 } else {
-                    if (HS) k_adj_rhs<real, false, true><<<grid_for(N), kAT, 0, st>>>(X[j], hs, Kst[j], g.nx, g.ny, g.nz, J, twoD, H0, H1, H2, lamb, dt);
-                    else k_adj_rhs<real, false, false><<<grid_for(N), kAT, 0, st>>>(X[j], nullptr, Kst[j], g.nx, g.ny, g.nz, J, twoD, H0, H1, H2, lamb, dt);
+                    if (HS) k_adj_rhs<real, false, true><<<grid_for(N), kAT, 0, st>>>(X[j], hs, Kst[j], g.nx, g.ny, g.nz, J, twoD, H0, H1, H2, lamb, dt, A.bc);
+                    else k_adj_rhs<real, false, false><<<grid_for(N), kAT, 0, st>>>(X[j], nullptr, Kst[j], g.nx, g.ny, g.nz, J, twoD, H0, H1, H2, lamb, dt, A.bc);
                 }
             }
             {
@@ -510,11 +540,11 @@ cudaError_t adjoint_run(const AdjointRun<real>& A) {
             k_adj_top<real><<<grid_for(N), kAT, 0, st>>>(ta, N);
             for (int j = S - 1; j >= 0; --j) {
                 if (A.precession) {
-                    if (HS) k_adj_w<real, true, true><<<nb, kAT, 0, st>>>(X[j], hs, LK[j], w, u, A.g_h, partials, g.nx, g.ny, g.nz, J, twoD, H0, H1, H2, lamb, dt);
-                    else k_adj_w<real, true, false><<<nb, kAT, 0, st>>>(X[j], nullptr, LK[j], w, u, A.g_h, partials, g.nx, g.ny, g.nz, J, twoD, H0, H1, H2, lamb, dt);
+                    if (HS) k_adj_w<real, true, true><<<nb, kAT, 0, st>>>(X[j], hs, LK[j], w, u, A.g_h, partials, g.nx, g.ny, g.nz, J, twoD, H0, H1, H2, lamb, dt, A.bc);
+                    else k_adj_w<real, true, false><<<nb, kAT, 0, st>>>(X[j], nullptr, LK[j], w, u, A.g_h, partials, g.nx, g.ny, g.nz, J, twoD, H0, H1, H2, lamb, dt, A.bc);
                 } else {
-                    if (HS) k_adj_w<real, false, true><<<nb, kAT, 0, st>>>(X[j], hs, LK[j], w, u, A.g_h, partials, g.nx, g.ny, g.nz, J, twoD, H0, H1, H2, lamb, dt);
-                    else k_adj_w<real, false, false><<<nb, kAT, 0, st>>>(X[j], nullptr, LK[j], w, u, A.g_h, partials, g.nx, g.ny, g.nz, J, twoD, H0, H1, H2, lamb, dt);
+                    if (HS) k_adj_w<real, false, true><<<nb, kAT, 0, st>>>(X[j], hs, LK[j], w, u, A.g_h, partials, g.nx, g.ny, g.nz, J, twoD, H0, H1, H2, lamb, dt, A.bc);
+                    else k_adj_w<real, false, false><<<nb, kAT, 0, st>>>(X[j], nullptr, LK[j], w, u, A.g_h, partials, g.nx, g.ny, g.nz, J, twoD, H0, H1, H2, lamb, dt, A.bc);
                 }
                 XArgs<real> xa{};
                 xa.w = w;
@@ -527,6 +557,7 @@ cudaError_t adjoint_run(const AdjointRun<real>& A) {
                 xa.nl = j;
                 xa.J = J;
                 xa.twoD = twoD;
+                xa.bc = A.bc;
                 k_adj_x<real><<<grid_for(N), kAT, 0, st>>>(xa, g.nx, g.ny, g.nz);
             }
             if ((e = cudaGetLastError()) != cudaSuccess) return e;

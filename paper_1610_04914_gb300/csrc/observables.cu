@@ -29,7 +29,8 @@ __global__ void __launch_bounds__(kObsThreads) k_obs_partial(const real* __restr
                                                              const real* __restrict__ sz, const real* __restrict__ hx,
                                                              const real* __restrict__ hy, const real* __restrict__ hz,
                                                              int nx, int ny, int nz, double J, double D, double H0,
-                                                             double H1, double H2, double* __restrict__ partials) {
+                                                             double H1, double H2, double* __restrict__ partials,
+                                                             int bc) {
     // one warp per lattice row (y, z); lanes stride along x, so no per-site
     // index division and the row's loads are coalesced
     const long long P = (long long)nx * ny;
@@ -58,8 +59,12 @@ __global__ void __launch_bounds__(kObsThreads) k_obs_partial(const real* __restr
             rm0 += a;
             rm1 += b;
             rm2 += c;
-            const real bond = a * (sx[ix] + sx[iy] + sx[iz]) + b * (sy[ix] + sy[iy] + sy[iz]) +
-                              c * (sz[ix] + sz[iy] + sz[iz]);
+            // forward bonds; with free boundaries none crosses the last face
+            const real wx = (bc && x + 1 == nx) ? real(0) : real(1);
+            const real wy = (bc && y + 1 == ny) ? real(0) : real(1);
+            const real wz = (bc && z + 1 == nz) ? real(0) : real(1);
+            const real bond = a * (wx * sx[ix] + wy * sx[iy] + wz * sx[iz]) + b * (wx * sy[ix] + wy * sy[iy] + wz * sy[iz]) +
+                              c * (wx * sz[ix] + wy * sz[iy] + wz * sz[iz]);
             real f0 = H0r, f1 = H1r, f2 = H2r;
             if (HSITE) {
                 f0 += hx[i];
@@ -248,16 +253,16 @@ int observables_blocks(Geom g) {
 template <typename real>
 cudaError_t launch_observables(const real* s[3], const real* hs[3], Geom g, Phys<double> ph, double* partials,
                                int nblocks, double* out5, double* sample_ring, int ring, long long* d_interval,
-                               long long* d_sample_count, int R, cudaStream_t stream) {
+                               long long* d_sample_count, int R, cudaStream_t stream, int bc) {
     const double D = 0.5 * ph.twoD;
     if (hs[0])
         k_obs_partial<real, true><<<nblocks, kObsThreads, 0, stream>>>(s[0], s[1], s[2], hs[0], hs[1], hs[2], g.nx, g.ny, g.nz,
                                                                        (double)ph.J, D, (double)ph.H[0], (double)ph.H[1],
-                                                                       (double)ph.H[2], partials);
+                                                                       (double)ph.H[2], partials, bc);
     else
         k_obs_partial<real, false><<<nblocks, kObsThreads, 0, stream>>>(s[0], s[1], s[2], nullptr, nullptr, nullptr, g.nx, g.ny,
                                                                         g.nz, (double)ph.J, D, (double)ph.H[0],
-                                                                        (double)ph.H[1], (double)ph.H[2], partials);
+                                                                        (double)ph.H[1], (double)ph.H[2], partials, bc);
     k_obs_final<<<1, kObsThreads, 0, stream>>>(partials, nblocks, g.N(), out5, sample_ring, ring, d_interval,
                                                d_sample_count, R);
     return cudaGetLastError();
@@ -275,9 +280,10 @@ cudaError_t launch_observables_batch(const float* s[3], const BatchRep* reps, co
 }
 
 template cudaError_t launch_observables<float>(const float* s[3], const float* hs[3], Geom, Phys<double>, double*, int,
-                                               double*, double*, int, long long*, long long*, int, cudaStream_t);
+                                               double*, double*, int, long long*, long long*, int, cudaStream_t, int);
 template cudaError_t launch_observables<double>(const double* s[3], const double* hs[3], Geom, Phys<double>, double*,
-                                                int, double*, double*, int, long long*, long long*, int, cudaStream_t);
+                                                int, double*, double*, int, long long*, long long*, int, cudaStream_t,
+                                                int);
 
 }  // namespace spin
 

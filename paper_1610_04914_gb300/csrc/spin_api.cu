@@ -71,7 +71,7 @@ int validate(const spin_params* p) {
     if (!std::isfinite(p->J) || !std::isfinite(p->D)) return SPIN_EINVAL;
     for (int a = 0; a < 3; ++a)
         if (!std::isfinite(p->H[a])) return SPIN_EINVAL;
-    if (p->path < 0 || p->path > 1 || p->reserved != 0) return SPIN_EINVAL;
+    if (p->path < 0 || p->path > 1 || p->bc < 0 || p->bc > 1) return SPIN_EINVAL;
     if (p->replica < 0) return SPIN_EINVAL;
     return SPIN_OK;
 }
@@ -149,6 +149,7 @@ StepLaunch<real> make_launch(spin_lattice* h, int from, bool pulse) {
     L.tmp = static_cast<real*>(h->tmp);
     L.stream = h->st;
     L.force_generic = h->p.path == 1;
+    L.bc = h->p.bc;
     return L;
 }
 
@@ -168,13 +169,15 @@ cudaError_t observe(spin_lattice* h, int b, bool sample, cudaStream_t st) {
         const float* hs[3] = {(const float*)h->hs[0], (const float*)h->hs[1], (const float*)h->hs[2]};
         return launch_observables<float>(s, hs, h->g, phys64(h), h->partials, h->nblocks_obs,
                                          sample ? h->out_sample : h->out_obs, sample ? h->ring : nullptr,
-                                         SPIN_SAMPLE_RING, h->d_interval, h->d_sample_count, h->p.steps_per_pulse, st);
+                                         SPIN_SAMPLE_RING, h->d_interval, h->d_sample_count, h->p.steps_per_pulse, st,
+                                         h->p.bc);
     }
     const double* s[3] = {(const double*)h->buf[b][0], (const double*)h->buf[b][1], (const double*)h->buf[b][2]};
     const double* hs[3] = {(const double*)h->hs[0], (const double*)h->hs[1], (const double*)h->hs[2]};
     return launch_observables<double>(s, hs, h->g, phys64(h), h->partials, h->nblocks_obs,
                                       sample ? h->out_sample : h->out_obs, sample ? h->ring : nullptr,
-                                      SPIN_SAMPLE_RING, h->d_interval, h->d_sample_count, h->p.steps_per_pulse, st);
+                                      SPIN_SAMPLE_RING, h->d_interval, h->d_sample_count, h->p.steps_per_pulse, st,
+                                      h->p.bc);
 }
 
 // One step n -> n+1 from buffer `from` on stream st (no host bookkeeping).
@@ -251,6 +254,7 @@ int backward_t(spin_lattice* h, const double dLdM[3], double dLdE, void* ws, dou
     A.noise = h->p.noise;
     A.precession = h->p.precession;
     A.renorm = h->p.renorm;
+    A.bc = h->p.bc;
     A.seed = h->p.seed;
     A.replica = (uint64_t)h->p.replica;
     A.sigma = std::sqrt(2.0 * h->p.lambda * h->p.T * h->p.steps_per_pulse * std::fabs(h->p.dt));

@@ -49,6 +49,7 @@ struct StepLaunch {
     real* tmp;             // generic path: (stages + 1) * 3N scratch
     cudaStream_t stream;
     int force_generic;
+    int bc;                // 0 periodic, 1 free boundaries
 };
 
 template <typename real>
@@ -102,7 +103,7 @@ template <typename real>
 cudaError_t launch_observables(const real* s[3], const real* hs[3], Geom g, Phys<double> ph,
                                double* partials, int nblocks, double* out5, double* sample_ring,
                                int ring, long long* d_interval, long long* d_sample_count, int R,
-                               cudaStream_t stream);
+                               cudaStream_t stream, int bc = 0);
 int observables_blocks(Geom g);
 
 cudaError_t launch_noise_draw(uint64_t seed, long long k, long long replica, long long n, int precision,
@@ -117,7 +118,7 @@ struct AdjointRun {
     const Tableau* tab;
     int K;                   // checkpoint interval (steps)
     long long n0, n_end;     // recorded range: states n0 .. n_end
-    int R, noise, precession, renorm;
+    int R, noise, precession, renorm, bc;
     uint64_t seed, replica;
     double sigma, J, D, H[3], lambda, dt;
     const real* h_site;      // component-major 3N or null

@@ -102,6 +102,7 @@ struct ChainArgs {
     uint64_t seed, replica;
     real sigma;
     const long long* interval;
+    int bc;  // 1: free boundaries (outside columns and planes are zero spins)
 };
 
 // Register rings, indexed by (local plane index) & 3.
@@ -117,7 +118,7 @@ template <typename real, int S, int BX, int BY, bool PREC, bool HSITE, bool PULS
 __device__ __forceinline__ void chain_iteration(const ChainArgs<real>& a, Rings<real, S, HSITE>& r,
                                                 real* __restrict__ sh, int i, int t0, int z0, int col,
                                                 int plane, bool out_col, int tx, int ty, int xm, int xp,
-                                                int ym, int yp, long long k) {
+                                                int ym, int yp, long long k, real cmask) {
     constexpr int TILE = BX * BY;
     const int buf = P & 1;
     real* shb = sh + buf * (S * 3 * TILE);
@@ -143,6 +144,12 @@ __device__ __forceinline__ void chain_iteration(const ChainArgs<real>& a, Rings<
         r.s[slot][0] = __ldg(a.in0 + off);
         r.s[slot][1] = __ldg(a.in1 + off);
         r.s[slot][2] = __ldg(a.in2 + off);
+        if (a.bc) {
+            const real m = (t + S >= 0 && t + S < a.nz) ? cmask : real(0);
+            r.s[slot][0] *= m;
+            r.s[slot][1] *= m;
+            r.s[slot][2] *= m;
+        }
         if (HSITE) {
             const int gzh = wrap_index(t + S - 1, a.nz);
             const long long offh = (long long)gzh * plane + col;
@@ -225,6 +232,7 @@ __global__ void __launch_bounds__(BX* BY, 1) k_step_chain(ChainArgs<real> a) {
     const int z0 = (int)blockIdx.z * a.tz;
     const int t0 = z0 - 2 * S + 2;
     const long long k = PULSE ? *a.interval : 0;
+    const real cmask = (a.bc && (gxu < 0 || gxu >= a.nx || gyu < 0 || gyu >= a.ny)) ? real(0) : real(1);
 
     Rings<real, S, HSITE> r;
 #pragma unroll
@@ -244,13 +252,19 @@ __global__ void __launch_bounds__(BX* BY, 1) k_step_chain(ChainArgs<real> a) {
         r.s[L & 3][0] = __ldg(a.in0 + off);
         r.s[L & 3][1] = __ldg(a.in1 + off);
         r.s[L & 3][2] = __ldg(a.in2 + off);
+        if (a.bc) {
+            const real m = (t0 + L >= 0 && t0 + L < a.nz) ? cmask : real(0);
+            r.s[L & 3][0] *= m;
+            r.s[L & 3][1] *= m;
+            r.s[L & 3][2] *= m;
+        }
     }
 
     for (int i = 0; i < a.n_iter; i += 4) {
-        chain_iteration<real, S, BX, BY, PREC, HSITE, PULSE, 0>(a, r, sh, i + 0, t0, z0, col, plane, out_col, tx, ty, xm, xp, ym, yp, k);
-        chain_iteration<real, S, BX, BY, PREC, HSITE, PULSE, 1>(a, r, sh, i + 1, t0, z0, col, plane, out_col, tx, ty, xm, xp, ym, yp, k);
-        chain_iteration<real, S, BX, BY, PREC, HSITE, PULSE, 2>(a, r, sh, i + 2, t0, z0, col, plane, out_col, tx, ty, xm, xp, ym, yp, k);
-        chain_iteration<real, S, BX, BY, PREC, HSITE, PULSE, 3>(a, r, sh, i + 3, t0, z0, col, plane, out_col, tx, ty, xm, xp, ym, yp, k);
+        chain_iteration<real, S, BX, BY, PREC, HSITE, PULSE, 0>(a, r, sh, i + 0, t0, z0, col, plane, out_col, tx, ty, xm, xp, ym, yp, k, cmask);
+        chain_iteration<real, S, BX, BY, PREC, HSITE, PULSE, 1>(a, r, sh, i + 1, t0, z0, col, plane, out_col, tx, ty, xm, xp, ym, yp, k, cmask);
+        chain_iteration<real, S, BX, BY, PREC, HSITE, PULSE, 2>(a, r, sh, i + 2, t0, z0, col, plane, out_col, tx, ty, xm, xp, ym, yp, k, cmask);
+        chain_iteration<real, S, BX, BY, PREC, HSITE, PULSE, 3>(a, r, sh, i + 3, t0, z0, col, plane, out_col, tx, ty, xm, xp, ym, yp, k, cmask);
     }
 }
 
@@ -349,6 +363,7 @@ static cudaError_t launch_chain(const StepLaunch<real>& L) {
     a.replica = L.replica;
     a.sigma = L.sigma;
     a.interval = L.d_interval;
+    a.bc = L.bc;
     const int tiles_x = (L.g.nx + (BX - 2 * S) - 1) / (BX - 2 * S);
     const int tiles_y = (L.g.ny + (BY - 2 * S) - 1) / (BY - 2 * S);
     // z chunk: enough CTAs to fill the GPU twice over, chunks of >= 8 planes
@@ -378,7 +393,7 @@ struct Vec3P {
 // K = dt f(x) over the lattice; neighbours read from global memory.
 template <typename real, bool PREC, bool HSITE>
 __global__ void k_stage_rhs(Vec3P<real> x, Vec3P<real> hs, real* __restrict__ K0, real* __restrict__ K1,
-                            real* __restrict__ K2, int nx, int ny, int nz, Phys<real> ph, real dt) {
+                            real* __restrict__ K2, int nx, int ny, int nz, Phys<real> ph, real dt, int bc) {
     const long long N = (long long)nx * ny * nz;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
          i += (long long)gridDim.x * blockDim.x) {
@@ -392,11 +407,16 @@ __global__ void k_stage_rhs(Vec3P<real> x, Vec3P<real> hs, real* __restrict__ K0
                                  (long long)zi * P + (long long)wrap_index(yi + 1, ny) * nx + xi,
                                  (long long)wrap_index(zi - 1, nz) * P + (long long)yi * nx + xi,
                                  (long long)wrap_index(zi + 1, nz) * P + (long long)yi * nx + xi};
+        // free boundaries: a neighbour across a face does not exist
+        const real w[6] = {(bc && xi == 0) ? real(0) : real(1), (bc && xi == nx - 1) ? real(0) : real(1),
+                           (bc && yi == 0) ? real(0) : real(1), (bc && yi == ny - 1) ? real(0) : real(1),
+                           (bc && zi == 0) ? real(0) : real(1), (bc && zi == nz - 1) ? real(0) : real(1)};
         real h[3], s[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const real* q = x.p[c];
-            const real sum = q[nb[0]] + q[nb[1]] + q[nb[2]] + q[nb[3]] + q[nb[4]] + q[nb[5]];
+            const real sum = w[0] * q[nb[0]] + w[1] * q[nb[1]] + w[2] * q[nb[2]] + w[3] * q[nb[3]] + w[4] * q[nb[4]] +
+                             w[5] * q[nb[5]];
             h[c] = ph.J * sum + ph.H[c];
             if (HSITE) h[c] += hs.p[c][i];
             s[c] = q[i];
@@ -483,14 +503,14 @@ static cudaError_t launch_generic(const StepLaunch<real>& L) {
         real* k0 = K[j];
         if (L.precession) {
             if (hs)
-                k_stage_rhs<real, true, true><<<blocks, threads, 0, L.stream>>>(xv, hv, k0, k0 + N, k0 + 2 * N, L.g.nx, L.g.ny, L.g.nz, L.ph, (real)L.dt);
+                k_stage_rhs<real, true, true><<<blocks, threads, 0, L.stream>>>(xv, hv, k0, k0 + N, k0 + 2 * N, L.g.nx, L.g.ny, L.g.nz, L.ph, (real)L.dt, L.bc);
             else
-                k_stage_rhs<real, true, false><<<blocks, threads, 0, L.stream>>>(xv, hv, k0, k0 + N, k0 + 2 * N, L.g.nx, L.g.ny, L.g.nz, L.ph, (real)L.dt);
+                k_stage_rhs<real, true, false><<<blocks, threads, 0, L.stream>>>(xv, hv, k0, k0 + N, k0 + 2 * N, L.g.nx, L.g.ny, L.g.nz, L.ph, (real)L.dt, L.bc);
         } else {
             if (hs)
-                k_stage_rhs<real, false, true><<<blocks, threads, 0, L.stream>>>(xv, hv, k0, k0 + N, k0 + 2 * N, L.g.nx, L.g.ny, L.g.nz, L.ph, (real)L.dt);
+                k_stage_rhs<real, false, true><<<blocks, threads, 0, L.stream>>>(xv, hv, k0, k0 + N, k0 + 2 * N, L.g.nx, L.g.ny, L.g.nz, L.ph, (real)L.dt, L.bc);
             else
-                k_stage_rhs<real, false, false><<<blocks, threads, 0, L.stream>>>(xv, hv, k0, k0 + N, k0 + 2 * N, L.g.nx, L.g.ny, L.g.nz, L.ph, (real)L.dt);
+                k_stage_rhs<real, false, false><<<blocks, threads, 0, L.stream>>>(xv, hv, k0, k0 + N, k0 + 2 * N, L.g.nx, L.g.ny, L.g.nz, L.ph, (real)L.dt, L.bc);
         }
     }
     CombineArgs<real> c{};

@@ -66,6 +66,7 @@ struct PatchArgs {
     uint64_t seed, replica;
     float sigma;
     const long long* interval;
+    int bc;            // 1: free boundaries (outside columns and planes read as zero spins)
 };
 
 typedef float2 f2;
@@ -113,6 +114,7 @@ struct PThread {
     int plane;         // nx*ny
     int gz_issue;      // wrapped z of the next plane to prefetch (t+S+2)
     int gz_field;      // wrapped z of the next site-field plane (t+S-1)
+    f2 cmask[PY];      // 1 for lattice columns, 0 for columns outside a free-boundary lattice
 };
 
 // Per-thread staging ring for spin planes fetched two iterations ahead with
@@ -178,6 +180,17 @@ __device__ __forceinline__ void patch_iteration(const PatchArgs& a, PRings<S, HS
             for (int c = 0; c < 3; ++c)
                 r.s[slot][rr][c] = make_float2(*stage_slot<S>(stg, slot, c, rr, 0, tid),
                                                *stage_slot<S>(stg, slot, c, rr, 1, tid));
+        if (a.bc) {
+            // free boundaries: no spin outside the lattice (a zero spin stays
+            // zero through every stage, so it never feeds the stencil)
+            const float zin = (t + S >= 0 && t + S < a.nz) ? 1.f : 0.f;
+#pragma unroll
+            for (int rr = 0; rr < PY; ++rr) {
+                const f2 m = make_float2(th.cmask[rr].x * zin, th.cmask[rr].y * zin);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) r.s[slot][rr][c] = mul2(r.s[slot][rr][c], m);
+            }
+        }
         if (HSITE) {
             const long long bh = (long long)th.gz_field * th.plane;
             th.gz_field = th.gz_field + 1 == a.nz ? 0 : th.gz_field + 1;
@@ -322,6 +335,9 @@ __device__ __forceinline__ void patch_tile(const PatchArgs& a, int bx, int by, i
             const int gxu = bx * OUTX - S + cx;
             th.col[rr][e] = gy * a.nx + wrapi(gxu, a.nx);
             th.out[rr][e] = cx >= S && cx < kPC - S && cy >= S && cy < ROWS - S && gxu < a.nx && gyu < a.ny;
+            const float in = (gxu >= 0 && gxu < a.nx && gyu >= 0 && gyu < a.ny) ? 1.f : 0.f;
+            if (e == 0) th.cmask[rr].x = a.bc ? in : 1.f;
+            else th.cmask[rr].y = a.bc ? in : 1.f;
         }
     }
     const int z0 = bz * a.tz;
@@ -350,6 +366,12 @@ __device__ __forceinline__ void patch_tile(const PatchArgs& a, int bx, int by, i
             r.s[L & 3][rr][0] = make_float2(__ldg(a.in0 + o0), __ldg(a.in0 + o1));
             r.s[L & 3][rr][1] = make_float2(__ldg(a.in1 + o0), __ldg(a.in1 + o1));
             r.s[L & 3][rr][2] = make_float2(__ldg(a.in2 + o0), __ldg(a.in2 + o1));
+            if (a.bc) {
+                const float zin = (t0 + L >= 0 && t0 + L < a.nz) ? 1.f : 0.f;
+                const f2 m = make_float2(th.cmask[rr].x * zin, th.cmask[rr].y * zin);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) r.s[L & 3][rr][c] = mul2(r.s[L & 3][rr][c], m);
+            }
         }
     }
     // planes S and S+1 (local) go to the staging ring before the march
@@ -498,6 +520,7 @@ PatchArgs patch_args_common(const StepLaunch<float>& L) {
     a.replica = L.replica;
     a.sigma = L.sigma;
     a.interval = L.d_interval;
+    a.bc = L.bc;
     return a;
 }
 

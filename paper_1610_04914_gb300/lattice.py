@@ -37,6 +37,7 @@ class Params:
     replica: int = 0
     precision: int = 32
     path: int = 0
+    bc: int = 0            # 0: periodic, 1: free boundaries
 
     @property
     def N(self) -> int:
@@ -49,7 +50,7 @@ class Params:
     def c(self) -> B.spin_params:
         return B.spin_params(self.nx, self.ny, self.nz, self.precision, self.integrator,
                              self.precession, self.R, self.renorm, self.noise, self.replica,
-                             self.path, 0, self.J, self.D, (ctypes.c_double * 3)(*self.H),
+                             self.path, self.bc, self.J, self.D, (ctypes.c_double * 3)(*self.H),
                              self.lam, self.T, self.dt, self.seed & 0xFFFFFFFFFFFFFFFF)
 
 

@@ -8,7 +8,7 @@ def orc_params(orc, p, **over):
     """Oracle parameters for the same problem as GPU parameters p."""
     kw = dict(J=p.J, D=p.D, H=tuple(p.H), lam=p.lam, T=p.T, dt=p.dt, R=p.R,
               integrator=p.integrator, precession=p.precession, renorm=p.renorm,
-              seed=p.seed, replica=p.replica)
+              seed=p.seed, replica=p.replica, bc=p.bc)
     kw.update(over)
     return orc.Params(p.nx, p.ny, p.nz, **kw)
 
