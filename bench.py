@@ -49,6 +49,43 @@ def _dist():
     return ws, rank, local
 
 
+def time_plain_steps(torch, lat, R, intervals, stream, flush):
+    """Per-launch milliseconds of the plain fused step: CUDA events on the
+    launching stream around each run of consecutive plain steps of an
+    interval (the pulse step also launches the pulse kernel, the last step the
+    reduction), L2 flushed before each interval, and a sleep kernel in front so
+    the host has queued the launches and the events bracket back-to-back
+    kernels rather than host latency.  Each timed run is one call of an even
+    number of steps: a call that ends on an odd step count copies the state
+    back into the caller's buffer, which is not part of a step."""
+    runs = []
+    with torch.cuda.stream(stream):
+        for _ in range(intervals):
+            flush.zero_()
+            torch.cuda._sleep(3_000_000)
+            q = 0
+            while q < R:
+                if (q + 1) % R != 0 and (q + 1) % R != R // 2:
+                    j = q
+                    while j < R and (j + 1) % R != 0 and (j + 1) % R != R // 2:
+                        j += 1
+                    even = (j - q) & ~1
+                    if even:
+                        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        a.record(stream)
+                        lat.step(even)
+                        b.record(stream)
+                        runs.append((a, b, even))
+                    if j - q - even:
+                        lat.step(j - q - even)
+                    q = j
+                else:
+                    lat.step(1)
+                    q += 1
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) / n for a, b, n in runs for _ in range(n)]
+
+
 def whole_job_rate(t_local_s: float, units_local: float):
     """Whole-job throughput of independent replicas, one per rank: units summed
     over ranks divided by the slowest rank's timed duration.  Returns
@@ -289,19 +326,7 @@ def kernel_timing_256(sp, torch, dev, flush, stream, hbm_peak):
     with torch.cuda.stream(stream):
         lat = sp.Lattice(p, torch.from_numpy(s0), device=dev, stream=stream)
         lat.step(p.R)
-        ev = []
-        for _ in range(2):
-            flush.zero_()
-            torch.cuda._sleep(3_000_000)
-            for q in range(p.R):
-                a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                lat.step(1)
-                c.record(stream)
-                if (q + 1) % p.R != 0 and (q + 1) % p.R != p.R // 2:
-                    ev.append((a, c))
-    torch.cuda.synchronize()
-    ms = float(np.mean([a.elapsed_time(c) for a, c in ev]))
+    ms = float(np.mean(time_plain_steps(torch, lat, p.R, 2, stream, flush)))
     lat.close()
     gbs = BYTES_PER_SPIN_STEP_FP32 * p.N / (ms / 1e3) / 1e9
     return {"lattice": "256^3", "kernel_ms_per_launch": ms, "achieved_GBps": gbs, "frac": gbs / hbm_peak,
@@ -388,29 +413,13 @@ def run_ours(args, ws, rank, local):
     clk = clocks.stop()
     value, t_dev, _ = whole_job_rate(sum(step_ms) / 1e3, N * R * args.steps)
 
-    # dominant kernel: the fused RK4 step, timed launch by launch with events
-    # on the launching stream.  A sleep kernel first lets the host queue the
-    # whole interval, so the events bracket back-to-back kernels and not the
-    # host's launch latency.
-    kern_ms = []
-    with torch.cuda.stream(stream):
-        for k in range(max(3, args.steps)):
-            flush.zero_()
-            torch.cuda._sleep(3_000_000)
-            evs = []
-            for q in range(R):
-                a, bb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                lat.step(1)
-                bb.record(stream)
-                # plain steps only: the sample step also launches the reduction
-                # and the pulse step is a different kernel instance
-                if (q + 1) % R != 0 and (q + 1) % R != R // 2:
-                    evs.append((a, bb))
-            kern_ms.extend(evs)
-    torch.cuda.synchronize()
-    kt = [a.elapsed_time(bb) for a, bb in kern_ms]
-    t_kernel = float(np.mean(kt)) / 1e3
+    # dominant kernel: the fused RK4 step (plain steps), timed with CUDA events
+    # on the launching stream around runs of consecutive plain launches
+    # (steps 1-4 and 6-9 of each interval: step 5 carries the pulse kernel,
+    # step 10 the reduction).  A sleep kernel first lets the host queue the
+    # interval, so the events bracket back-to-back kernels, not host latency.
+    kern_ms = time_plain_steps(torch, lat, R, max(3, args.steps), stream, flush)
+    t_kernel = float(np.mean(kern_ms)) / 1e3
     hbm_peak, peak_src = _measured_peaks()
     achieved_gbs = BYTES_PER_SPIN_STEP_FP32 * N / t_kernel / 1e9
     achieved_tflops = RK4_FLOPS_PER_SPIN_STEP * N / t_kernel / 1e12

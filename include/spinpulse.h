@@ -253,6 +253,59 @@ int spin_batch_destroy(spin_batch* b);
 const char* spin_batch_last_error(const spin_batch* b);
 
 /*
+ * Single-spin replicas (paper Sec. III: a spin in a field, Eq. s_evolution_anal
+ * and Fig. 4; a uniaxial spin in a transverse field and its thermally
+ * activated escape, Sec. III.B and Fig. 6).  nrep independent spins with
+ * energy E = -D s_z^2 - H.s (H_eff = H + 2D s_z z; J, nx, ny, nz, replica,
+ * path and bc of p are ignored), one GPU thread each, with the integrator,
+ * renormalisation and pulse schedule of spin_step_pulse.  Replica r has
+ * temperature T[r] and damping lambda[r] (host arrays of nrep values;
+ * lambda NULL: p->lambda for all).
+ *   s        device array of 3*nrep values of the state type: s_x of all
+ *            replicas, then s_y, then s_z; updated in place
+ *   scratch  device array of 2*nrep values of the state type, caller-owned,
+ *            receives the pulse angle scales and dampings
+ * Both calls upload those scales synchronously, then launch one kernel on
+ * cuda_stream and return without waiting for it.
+ * Errors: SPIN_EINVAL (bad sizes, pointers, parameters, T or lambda negative
+ * or non-finite), SPIN_ECUDA.
+ */
+
+/*
+ * spin_single_run: advance every replica from completed step n0 by nsteps
+ * steps; pulse k of replica r uses noise counter (0, k, r, 0), so replica r
+ * follows exactly a one-site lattice with replica index r and J = 0.
+ *   stop_on_crossing  1: a replica stops after the first step that leaves
+ *            s_z < 0 and stores that step number in first_passage[r]
+ *            (device int64, -1 = none yet; replicas with a stored step are
+ *            skipped by later calls) -- the first-passage procedure of
+ *            Sec. III.B
+ *   sz_sum, sz_count  nullable device arrays (FP64, int64) accumulating s_z
+ *            after every step with n mod R == 0 (equilibrium averages)
+ */
+int spin_single_run(const spin_params* p, int32_t nrep, const double* T, const double* lambda, void* s,
+                    void* scratch, int64_t n0, int64_t nsteps, int32_t stop_on_crossing, int64_t* first_passage,
+                    double* sz_sum, int64_t* sz_count, void* cuda_stream);
+
+/*
+ * spin_single_escape: renewal form of the first-passage procedure.  Every
+ * replica advances nsteps steps; when a step leaves s_z < 0 the replica adds
+ * the number of steps of its current trial to fpt_sum[r] (and its square to
+ * fpt_sq[r], nullable), increments fpt_count[r] and trial[r], and restarts
+ * from s_init (host, 3 values, s_init[2] >= 0) with its step count local_step[r]
+ * reset to 0.  Trial j of replica r uses noise counter (0, k, r + j*nrep, 0)
+ * with the pulse schedule counted from the start of the trial.  trial,
+ * local_step, fpt_sum, fpt_count: device int64 arrays of nrep values,
+ * zero-initialised by the caller before the first call, together with s set
+ * to s_init.  The mean first-passage time is sum(fpt_sum)/sum(fpt_count)
+ * steps.
+ */
+int spin_single_escape(const spin_params* p, int32_t nrep, const double* T, const double* lambda,
+                       const double* s_init, void* s, void* scratch, int64_t nsteps, int64_t* trial,
+                       int64_t* local_step, int64_t* fpt_sum, double* fpt_sq, int64_t* fpt_count,
+                       void* cuda_stream);
+
+/*
  * Observables of caller-owned spin arrays with no memory allocation at all.
  * The paper has no counterpart: this entry point serves callers that cannot
  * call cudaMalloc or ask their framework for memory where they need M and E

@@ -8,7 +8,7 @@ library with ``paper_1610_04914_gb300.build.build()``.
 """
 from ._binding import (HEUN, RK2_MIDPOINT, RK4, RK5_BUTCHER, SPIN_ENONFINITE, SPIN_OK,  # noqa: F401
                        SPIN_WARN_APPLICABILITY, SpinError, load)
-from .lattice import (Lattice, Params, SpinRunFn, spin_backward, spin_backward_workspace_size,  # noqa: F401
+from .lattice import (EscapeReplicas, Lattice, Params, SingleSpins, SpinRunFn, spin_backward, spin_backward_workspace_size,  # noqa: F401
                       spin_get_step, spin_lattice_create, spin_record_begin, spin_record_end,
                       spin_record_store_size,
                       spin_lattice_destroy, spin_noise_draw, spin_observables, spin_observables_noalloc, spin_samples,

@@ -1,0 +1,367 @@
+// Single-spin replicas (paper Sec. III: a spin in a field, and a uniaxial spin
+// in a transverse field with its thermally activated escape, Sec. III.B).
+// One thread owns one replica and integrates it through many steps in
+// registers, with the pulse noise of Eqs. (phi_n) and (s_rotation) once per
+// noise interval.  Two kernels:
+//   k_single_run     a fixed stretch of steps on the global step count n,
+//                    optionally stopping at the first step after which
+//                    s_z < 0 (the paper's first-passage procedure) and
+//                    optionally summing s_z at the end of every interval
+//                    (equilibrium averages, Fig. 4);
+//   k_single_escape  renewal form of the first-passage procedure: a replica
+//                    that crosses s_z = 0 records the passage time, restarts
+//                    from the initial state as a new trial and carries on,
+//                    so that no lane of a warp idles while the slowest trial
+//                    of the warp is still running.
+// The energy is E = -D s_z^2 - H.s, so H_eff = H + 2 D s_z z.  Noise counter
+// of pulse k: (0, k, r, 0) for replica r in the run kernel (a one-site
+// lattice with replica index r); (0, k, r + j nrep, 0) for trial j of replica
+// r in the escape kernel, k counted from the trial's start.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <vector>
+
+#include "../../include/spinpulse.h"
+#include "spin_device.cuh"
+#include "spin_internal.h"
+
+namespace spin {
+namespace {
+
+template <typename real>
+struct SingleCommon {
+    real* sx;
+    real* sy;
+    real* sz;
+    const real* sigma;   // per replica: sqrt(2 lambda_r T_r Delta t)
+    const real* lambda;  // per replica damping
+    int nrep, R, renorm, noise;
+    real D2, Hx, Hy, Hz, dt;
+    real a[6][6];
+    real b[6];
+    uint64_t seed;
+};
+
+// One step of the integrator with ST stages on one spin, then |s| = 1.
+template <typename real, bool PREC, int ST>
+__device__ __forceinline__ void single_step(real& s0, real& s1, real& s2, real lam, const SingleCommon<real>& C) {
+    real K[ST][3];
+#pragma unroll
+    for (int j = 0; j < ST; ++j) {
+        real x0 = s0, x1 = s1, x2 = s2;
+#pragma unroll
+        for (int l = 0; l < j; ++l) {
+            const real c = C.a[j][l];
+            x0 += c * K[l][0];
+            x1 += c * K[l][1];
+            x2 += c * K[l][2];
+        }
+        real f0, f1, f2;
+        llg_rhs<real, PREC>(x0, x1, x2, C.Hx, C.Hy, C.Hz + C.D2 * x2, lam, f0, f1, f2);
+        K[j][0] = C.dt * f0;
+        K[j][1] = C.dt * f1;
+        K[j][2] = C.dt * f2;
+    }
+#pragma unroll
+    for (int j = 0; j < ST; ++j) {
+        s0 += C.b[j] * K[j][0];
+        s1 += C.b[j] * K[j][1];
+        s2 += C.b[j] * K[j][2];
+    }
+    if (C.renorm) {
+        const real inv = Math<real>::rsqrt_(s0 * s0 + s1 * s1 + s2 * s2);
+        s0 *= inv;
+        s1 *= inv;
+        s2 *= inv;
+    }
+}
+
+template <typename real>
+struct RunArgs {
+    SingleCommon<real> c;
+    long long* first_passage;  // nullable; -1 = no passage yet
+    double* sz_sum;            // nullable
+    long long* sz_count;       // nullable with sz_sum
+    long long n0, nsteps;
+    int stop;
+};
+
+template <typename real, bool PREC, int ST>
+__global__ void __launch_bounds__(128) k_single_run(RunArgs<real> A) {
+    const SingleCommon<real>& C = A.c;
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= C.nrep) return;
+    long long fp = A.first_passage ? A.first_passage[r] : -1;
+    if (A.stop && fp >= 0) return;
+    real s0 = C.sx[r], s1 = C.sy[r], s2 = C.sz[r];
+    const real sig = C.sigma[r], lam = C.lambda[r];
+    double acc = 0.0;
+    long long cnt = 0;
+    // position in the pulse schedule, advanced without a division per step:
+    // ph = n mod R and kq = n div R for the step n just completed
+    int ph = (int)(A.n0 % C.R);
+    long long kq = A.n0 / C.R;
+    const int half = C.R / 2;
+    for (long long n = A.n0 + 1; n <= A.n0 + A.nsteps; ++n) {
+        single_step<real, PREC, ST>(s0, s1, s2, lam, C);
+        if (++ph == C.R) {
+            ph = 0;
+            ++kq;
+        }
+        // pulse number (n - 1) div R: kq, or kq - 1 when n is a multiple of R
+        if (C.noise && ph == half)
+            pulse_site<real>(s0, s1, s2, C.seed, 0ULL, (uint64_t)(ph == 0 ? kq - 1 : kq), (uint64_t)r, sig);
+        if (A.sz_sum && ph == 0) {
+            acc += (double)s2;
+            ++cnt;
+        }
+        if (A.stop && s2 < real(0)) {
+            fp = n;
+            break;
+        }
+    }
+    C.sx[r] = s0;
+    C.sy[r] = s1;
+    C.sz[r] = s2;
+    if (A.first_passage) A.first_passage[r] = fp;
+    if (A.sz_sum) {
+        A.sz_sum[r] += acc;
+        A.sz_count[r] += cnt;
+    }
+}
+
+template <typename real>
+struct EscapeArgs {
+    SingleCommon<real> c;
+    long long* trial;       // per replica: index j of the running trial
+    long long* local_step;  // per replica: steps completed in the running trial
+    long long* fpt_sum;     // per replica: sum of the passage steps of finished trials
+    double* fpt_sq;         // nullable: sum of their squares
+    long long* fpt_count;   // per replica: number of finished trials
+    real i0, i1, i2;        // initial state of every trial
+    long long nsteps;
+};
+
+template <typename real, bool PREC, int ST>
+__global__ void __launch_bounds__(128) k_single_escape(EscapeArgs<real> A) {
+    const SingleCommon<real>& C = A.c;
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= C.nrep) return;
+    real s0 = C.sx[r], s1 = C.sy[r], s2 = C.sz[r];
+    const real sig = C.sigma[r], lam = C.lambda[r];
+    long long j = A.trial[r], m = A.local_step[r];
+    long long fsum = 0, fcnt = 0;
+    double fsq = 0.0;
+    // ph = m mod R and kq = m div R, advanced without a division per step
+    int ph = (int)(m % C.R);
+    long long kq = m / C.R;
+    const int half = C.R / 2;
+    for (long long it = 0; it < A.nsteps; ++it) {
+        single_step<real, PREC, ST>(s0, s1, s2, lam, C);
+        ++m;
+        if (++ph == C.R) {
+            ph = 0;
+            ++kq;
+        }
+        if (C.noise && ph == half)
+            pulse_site<real>(s0, s1, s2, C.seed, 0ULL, (uint64_t)(ph == 0 ? kq - 1 : kq),
+                             (uint64_t)r + (uint64_t)j * (uint64_t)C.nrep, sig);
+        if (s2 < real(0)) {
+            fsum += m;
+            fsq += (double)m * (double)m;
+            ++fcnt;
+            ++j;
+            m = 0;
+            ph = 0;
+            kq = 0;
+            s0 = A.i0;
+            s1 = A.i1;
+            s2 = A.i2;
+        }
+    }
+    C.sx[r] = s0;
+    C.sy[r] = s1;
+    C.sz[r] = s2;
+    A.trial[r] = j;
+    A.local_step[r] = m;
+    A.fpt_sum[r] += fsum;
+    A.fpt_count[r] += fcnt;
+    if (A.fpt_sq) A.fpt_sq[r] += fsq;
+}
+
+template <typename real>
+SingleCommon<real> make_common(const spin_params* p, int nrep, void* s, void* scratch) {
+    SingleCommon<real> C{};
+    real* base = static_cast<real*>(s);
+    C.sx = base;
+    C.sy = base + nrep;
+    C.sz = base + 2 * (size_t)nrep;
+    C.sigma = static_cast<const real*>(scratch);
+    C.lambda = static_cast<const real*>(scratch) + nrep;
+    C.nrep = nrep;
+    C.R = p->steps_per_pulse;
+    C.renorm = p->renorm;
+    C.noise = p->noise;
+    const Tableau tb = tableau_for(p->integrator);
+    for (int j = 0; j < 6; ++j) {
+        C.b[j] = (real)tb.b[j];
+        for (int l = 0; l < 6; ++l) C.a[j][l] = (real)tb.a[j][l];
+    }
+    C.D2 = (real)(2.0 * p->D);
+    C.Hx = (real)p->H[0];
+    C.Hy = (real)p->H[1];
+    C.Hz = (real)p->H[2];
+    C.dt = (real)p->dt;
+    C.seed = p->seed;
+    return C;
+}
+
+template <typename real, bool PREC, int ST>
+struct RunK {
+    static void launch(int blocks, cudaStream_t st, const RunArgs<real>& A) {
+        k_single_run<real, PREC, ST><<<blocks, 128, 0, st>>>(A);
+    }
+};
+template <typename real, bool PREC, int ST>
+struct EscK {
+    static void launch(int blocks, cudaStream_t st, const EscapeArgs<real>& A) {
+        k_single_escape<real, PREC, ST><<<blocks, 128, 0, st>>>(A);
+    }
+};
+
+// Launch Kern<real, PREC, stages> for the integrator and precession flag.
+template <typename real, template <typename, bool, int> class Kern, typename Args>
+cudaError_t dispatch(const spin_params* p, int nrep, const Args& A, cudaStream_t st) {
+    const int blocks = (nrep + 127) / 128;
+    const int ns = tableau_for(p->integrator).stages;
+    const bool prec = p->precession != 0;
+#define SPIN_SINGLE_CASE(NS)                                  \
+    case NS:                                                  \
+        if (prec)                                             \
+            Kern<real, true, NS>::launch(blocks, st, A);      \
+        else                                                  \
+            Kern<real, false, NS>::launch(blocks, st, A);     \
+        break;
+    switch (ns) {
+        SPIN_SINGLE_CASE(2)
+        SPIN_SINGLE_CASE(4)
+        SPIN_SINGLE_CASE(6)
+        default:
+            return cudaErrorInvalidValue;
+    }
+#undef SPIN_SINGLE_CASE
+    return cudaGetLastError();
+}
+
+int check_single(const spin_params* p, int nrep, const double* T, const double* lambda, const void* s,
+                 const void* scratch) {
+    if (!p || nrep < 1 || !T || !s || !scratch) return SPIN_EINVAL;
+    if (p->precision != 32 && p->precision != 64) return SPIN_EINVAL;
+    if (p->steps_per_pulse < 1 || !std::isfinite(p->dt) || p->dt == 0.0) return SPIN_EINVAL;
+    if (p->integrator < 0 || p->integrator > 3) return SPIN_EINVAL;
+    if (!std::isfinite(p->D) || !std::isfinite(p->H[0]) || !std::isfinite(p->H[1]) || !std::isfinite(p->H[2]))
+        return SPIN_EINVAL;
+    for (int r = 0; r < nrep; ++r) {
+        const double lam = lambda ? lambda[r] : p->lambda;
+        if (!(T[r] >= 0.0) || !std::isfinite(T[r]) || !(lam >= 0.0) || !std::isfinite(lam)) return SPIN_EINVAL;
+    }
+    return SPIN_OK;
+}
+
+// Upload the per-replica pulse angle scales sqrt(2 lambda_r T_r Delta t)
+// (computed in FP64) and dampings into the caller's scratch.
+template <typename real>
+cudaError_t upload_scales(const spin_params* p, int nrep, const double* T, const double* lambda, void* scratch,
+                          cudaStream_t st) {
+    const double Dt = p->steps_per_pulse * std::fabs(p->dt);
+    std::vector<real> h(2 * (size_t)nrep);
+    for (int r = 0; r < nrep; ++r) {
+        const double lam = lambda ? lambda[r] : p->lambda;
+        h[r] = (real)std::sqrt(2.0 * lam * T[r] * Dt);
+        h[nrep + r] = (real)lam;
+    }
+    cudaError_t e = cudaMemcpyAsync(scratch, h.data(), sizeof(real) * h.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e;
+}
+
+template <typename real>
+cudaError_t run_t(const spin_params* p, int nrep, const double* T, const double* lambda, void* s, void* scratch,
+                  long long n0, long long nsteps, int stop, long long* fp, double* sz_sum, long long* sz_count,
+                  cudaStream_t st) {
+    cudaError_t e = upload_scales<real>(p, nrep, T, lambda, scratch, st);
+    if (e != cudaSuccess) return e;
+    RunArgs<real> A{};
+    A.c = make_common<real>(p, nrep, s, scratch);
+    A.first_passage = fp;
+    A.sz_sum = sz_sum;
+    A.sz_count = sz_count;
+    A.n0 = n0;
+    A.nsteps = nsteps;
+    A.stop = stop;
+    return dispatch<real, RunK>(p, nrep, A, st);
+}
+
+template <typename real>
+cudaError_t escape_t(const spin_params* p, int nrep, const double* T, const double* lambda, const double* s_init,
+                     void* s, void* scratch, long long nsteps, long long* trial, long long* local_step,
+                     long long* fpt_sum, double* fpt_sq, long long* fpt_count, cudaStream_t st) {
+    cudaError_t e = upload_scales<real>(p, nrep, T, lambda, scratch, st);
+    if (e != cudaSuccess) return e;
+    EscapeArgs<real> A{};
+    A.c = make_common<real>(p, nrep, s, scratch);
+    A.trial = trial;
+    A.local_step = local_step;
+    A.fpt_sum = fpt_sum;
+    A.fpt_sq = fpt_sq;
+    A.fpt_count = fpt_count;
+    A.i0 = (real)s_init[0];
+    A.i1 = (real)s_init[1];
+    A.i2 = (real)s_init[2];
+    A.nsteps = nsteps;
+    return dispatch<real, EscK>(p, nrep, A, st);
+}
+
+}  // namespace
+}  // namespace spin
+
+extern "C" int spin_single_run(const spin_params* p, int32_t nrep, const double* T, const double* lambda, void* s,
+                               void* scratch, int64_t n0, int64_t nsteps, int32_t stop_on_crossing,
+                               int64_t* first_passage, double* sz_sum, int64_t* sz_count, void* cuda_stream) {
+    using namespace spin;
+    const int chk = check_single(p, nrep, T, lambda, s, scratch);
+    if (chk != SPIN_OK) return chk;
+    if (n0 < 0 || nsteps < 0 || (sz_sum == nullptr) != (sz_count == nullptr)) return SPIN_EINVAL;
+    if (stop_on_crossing && !first_passage) return SPIN_EINVAL;
+    if (nsteps == 0) return SPIN_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const cudaError_t e =
+        p->precision == 64
+            ? run_t<double>(p, nrep, T, lambda, s, scratch, n0, nsteps, stop_on_crossing,
+                            (long long*)first_passage, sz_sum, (long long*)sz_count, st)
+            : run_t<float>(p, nrep, T, lambda, s, scratch, n0, nsteps, stop_on_crossing, (long long*)first_passage,
+                           sz_sum, (long long*)sz_count, st);
+    return e == cudaSuccess ? SPIN_OK : SPIN_ECUDA;
+}
+
+extern "C" int spin_single_escape(const spin_params* p, int32_t nrep, const double* T, const double* lambda,
+                                  const double* s_init, void* s, void* scratch, int64_t nsteps, int64_t* trial,
+                                  int64_t* local_step, int64_t* fpt_sum, double* fpt_sq, int64_t* fpt_count,
+                                  void* cuda_stream) {
+    using namespace spin;
+    const int chk = check_single(p, nrep, T, lambda, s, scratch);
+    if (chk != SPIN_OK) return chk;
+    if (!s_init || nsteps < 0 || !trial || !local_step || !fpt_sum || !fpt_count) return SPIN_EINVAL;
+    if (!std::isfinite(s_init[0]) || !std::isfinite(s_init[1]) || !std::isfinite(s_init[2]) || !(s_init[2] >= 0.0))
+        return SPIN_EINVAL;
+    if (nsteps == 0) return SPIN_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const cudaError_t e =
+        p->precision == 64
+            ? escape_t<double>(p, nrep, T, lambda, s_init, s, scratch, nsteps, (long long*)trial,
+                               (long long*)local_step, (long long*)fpt_sum, fpt_sq, (long long*)fpt_count, st)
+            : escape_t<float>(p, nrep, T, lambda, s_init, s, scratch, nsteps, (long long*)trial,
+                              (long long*)local_step, (long long*)fpt_sum, fpt_sq, (long long*)fpt_count, st);
+    return e == cudaSuccess ? SPIN_OK : SPIN_ECUDA;
+}

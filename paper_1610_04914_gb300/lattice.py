@@ -264,3 +264,98 @@ class SpinRunFn(torch.autograd.Function):
         return (torch.tensor(g["J"], dtype=torch.float64, device=dev),
                 torch.tensor(g["D"], dtype=torch.float64, device=dev),
                 g["h"].reshape(ctx.h_shape).to(ctx.h_dtype), None, None, None, None)
+
+
+
+def _host_doubles(vals):
+    vals = [float(v) for v in vals]
+    return (ctypes.c_double * len(vals))(*vals)
+
+
+class SingleSpins:
+    """nrep independent spins with E = -D s_z^2 - H.s at temperatures T[r]
+    and dampings lam[r] (default p.lam), one GPU thread each
+    (spin_single_run).  ``state`` is (3, nrep): s_x, s_y, s_z rows."""
+
+    def __init__(self, p: Params, T, state, lam=None, device="cuda", stream=None):
+        self.p = p
+        self.T = [float(v) for v in T]
+        self.nrep = len(self.T)
+        self.lam = None if lam is None else [float(v) for v in lam]
+        if self.lam is not None and len(self.lam) != self.nrep:
+            raise ValueError("lam must have one value per replica")
+        self.state = torch.as_tensor(state).to(device=device, dtype=p.dtype).reshape(3, self.nrep).clone()
+        self.scratch = torch.empty(2 * self.nrep, dtype=p.dtype, device=device)
+        self.first_passage = torch.full((self.nrep,), -1, dtype=torch.int64, device=device)
+        self.sz_sum = torch.zeros(self.nrep, dtype=torch.float64, device=device)
+        self.sz_count = torch.zeros(self.nrep, dtype=torch.int64, device=device)
+        self.n = 0
+        self.stream = stream
+
+    def run(self, nsteps: int, stop_on_crossing: bool = False, average: bool = False) -> "SingleSpins":
+        lam = None if self.lam is None else _host_doubles(self.lam)
+        check(B.load().spin_single_run(ctypes.byref(self.p.c()), self.nrep, _host_doubles(self.T), lam,
+                                       self.state.data_ptr(), self.scratch.data_ptr(), self.n, int(nsteps),
+                                       int(stop_on_crossing), self.first_passage.data_ptr(),
+                                       self.sz_sum.data_ptr() if average else None,
+                                       self.sz_count.data_ptr() if average else None, _stream_ptr(self.stream)))
+        self.n += int(nsteps)
+        return self
+
+
+class EscapeReplicas:
+    """Renewal first-passage runs (spin_single_escape): nrep replicas start
+    at ``s_init``; every crossing of s_z = 0 ends a trial, whose length in
+    steps is summed, and restarts the replica at ``s_init``."""
+
+    def __init__(self, p: Params, T, s_init, lam=None, device="cuda", stream=None):
+        self.p = p
+        self.T = [float(v) for v in T]
+        self.nrep = len(self.T)
+        self.lam = None if lam is None else [float(v) for v in lam]
+        if self.lam is not None and len(self.lam) != self.nrep:
+            raise ValueError("lam must have one value per replica")
+        self.s_init = [float(v) for v in s_init]
+        init = torch.tensor(self.s_init, dtype=torch.float64).reshape(3, 1).expand(3, self.nrep)
+        self.state = init.to(device=device, dtype=p.dtype).contiguous()
+        self.scratch = torch.empty(2 * self.nrep, dtype=p.dtype, device=device)
+        z = lambda dt: torch.zeros(self.nrep, dtype=dt, device=device)
+        self.trial, self.local_step = z(torch.int64), z(torch.int64)
+        self.fpt_sum, self.fpt_count, self.fpt_sq = z(torch.int64), z(torch.int64), z(torch.float64)
+        self.stream = stream
+
+    def run(self, nsteps: int) -> "EscapeReplicas":
+        lam = None if self.lam is None else _host_doubles(self.lam)
+        check(B.load().spin_single_escape(ctypes.byref(self.p.c()), self.nrep, _host_doubles(self.T), lam,
+                                          _host_doubles(self.s_init), self.state.data_ptr(),
+                                          self.scratch.data_ptr(), int(nsteps), self.trial.data_ptr(),
+                                          self.local_step.data_ptr(), self.fpt_sum.data_ptr(),
+                                          self.fpt_sq.data_ptr(), self.fpt_count.data_ptr(),
+                                          _stream_ptr(self.stream)))
+        return self
+
+    def mfpt(self, groups=None):
+        """Per group of replica indices (default: all replicas) a tuple
+        (mean first-passage time, its standard error, finished trials, rate),
+        times in time units.  ``rate`` = finished trials / total time run,
+        the unfinished trials included: for exponentially distributed
+        passage times it is the unbiased estimate of 1/MFPT even when the
+        run is not much longer than one passage time."""
+        torch.cuda.synchronize()
+        s = self.fpt_sum.double().cpu()
+        q = self.fpt_sq.cpu()
+        c = self.fpt_count.double().cpu()
+        open_steps = self.local_step.double().cpu()
+        dt = abs(self.p.dt)
+        out = []
+        for g in (groups if groups is not None else [list(range(self.nrep))]):
+            idx = torch.as_tensor(g, dtype=torch.long)
+            n = float(c[idx].sum())
+            total = float(s[idx].sum() + open_steps[idx].sum()) * dt
+            if n == 0:
+                out.append((float("inf"), float("inf"), 0, 0.0))
+                continue
+            m = float(s[idx].sum()) / n
+            var = max(float(q[idx].sum()) / n - m * m, 0.0)
+            out.append((m * dt, (var / n) ** 0.5 * dt, int(n), n / total))
+        return out if groups is not None else out[0]
