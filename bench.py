@@ -504,6 +504,17 @@ def run_ours(args, ws, rank, local):
     return 0
 
 
+ESCAPE = dict(D=1.0, h=0.5, lam=0.01, T=0.1, dt=1.0 / 6.0, R=6)
+
+
+def _escape_replicas(sp, nrep, precision):
+    """Renewal first-passage replicas of the escape workload (Sec. III.B)."""
+    w = ESCAPE
+    p = sp.Params(1, 1, 1, J=0.0, D=w["D"], H=(2 * w["h"] * w["D"], 0.0, 0.0), lam=w["lam"], T=w["T"], dt=w["dt"],
+                  R=w["R"], integrator=sp.RK5_BUTCHER, precession=1, seed=1, precision=precision)
+    return sp.EscapeReplicas(p, [w["T"]] * nrep, (w["h"], 0.0, (1 - w["h"] ** 2) ** 0.5))
+
+
 def run_profile_case(args):
     """A small fixed case for ncu: the benchmark's physics on an L^3 FP32
     lattice, advanced by single eager steps (step 5 of each interval carries
@@ -529,6 +540,26 @@ def run_profile_case(args):
     return 0
 
 
+def run_profile_single(args):
+    """A small fixed case for ncu: the escape workload of Sec. III.B (h = 1/2,
+    D = 1, lambda = 0.01, T = 0.1, Butcher RK5, delta t = 1/6, Delta t = 1,
+    FP32), nrep replicas, one warm-up launch of 100 steps then one launch of
+    --profile-steps steps."""
+    import torch
+
+    import paper_1610_04914_gb300 as sp
+    from paper_1610_04914_gb300 import build as b
+    b.build()
+    sp.load()
+    nrep = args.profile_single
+    e = _escape_replicas(sp, nrep, 32)
+    e.run(100)
+    e.run(args.profile_steps)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_single": nrep, "steps": args.profile_steps, "passages": int(e.fpt_count.sum())}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -540,10 +571,14 @@ def main():
     ap.add_argument("--profile-lattice", type=int, default=0,
                     help="profiling driver: L^3 FP32 RK4 lattice, --profile-steps single steps, no timing")
     ap.add_argument("--profile-steps", type=int, default=4)
+    ap.add_argument("--profile-single", type=int, default=0,
+                    help="profiling driver: escape workload with this many single-spin replicas, no timing")
     args = ap.parse_args()
     ws, rank, local = _dist()
     if args.profile_lattice:
         return run_profile_case(args)
+    if args.profile_single:
+        return run_profile_single(args)
     if args.impl == "reference":
         return run_reference(args, ws, rank)
     return run_ours(args, ws, rank, local)

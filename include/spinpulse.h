@@ -289,19 +289,23 @@ int spin_single_run(const spin_params* p, int32_t nrep, const double* T, const d
 
 /*
  * spin_single_escape: renewal form of the first-passage procedure.  Every
- * replica advances nsteps steps; when a step leaves s_z < 0 the replica adds
- * the number of steps of its current trial to fpt_sum[r] (and its square to
- * fpt_sq[r], nullable), increments fpt_count[r] and trial[r], and restarts
- * from s_init (host, 3 values, s_init[2] >= 0) with its step count local_step[r]
- * reset to 0.  Trial j of replica r uses noise counter (0, k, r + j*nrep, 0)
- * with the pulse schedule counted from the start of the trial.  trial,
- * local_step, fpt_sum, fpt_count: device int64 arrays of nrep values,
- * zero-initialised by the caller before the first call, together with s set
- * to s_init.  The mean first-passage time is sum(fpt_sum)/sum(fpt_count)
- * steps.
+ * replica advances nsteps steps from completed global step n0.  When a step
+ * leaves s_z < 0 the replica adds the number of steps of its current trial
+ * to fpt_sum[r] (and its square to fpt_sq[r], nullable), increments
+ * fpt_count[r] and trial[r], sets local_step[r] = -1 and waits until the
+ * next global step n with n mod R == 0 (at most R-1 steps); there it
+ * restarts from s_init (host, 3 values) with local_step[r] = 0.  Every trial
+ * thus starts at the beginning of a noise interval and sees the schedule of
+ * a fresh run; trial j of replica r uses noise counter (0, k, r + j*nrep, 0),
+ * k counted from the trial's start.  trial, local_step, fpt_sum, fpt_count:
+ * device int64 arrays of nrep values.  Start: all zero, s = s_init, n0 = 0
+ * (or any multiple of R); later calls pass n0 = steps completed so far.  A
+ * running replica whose local_step is out of phase with n0 (local_step mod
+ * R != n0 mod R) is treated as waiting.  The mean first-passage time is
+ * sum(fpt_sum)/sum(fpt_count) steps.
  */
 int spin_single_escape(const spin_params* p, int32_t nrep, const double* T, const double* lambda,
-                       const double* s_init, void* s, void* scratch, int64_t nsteps, int64_t* trial,
+                       const double* s_init, void* s, void* scratch, int64_t n0, int64_t nsteps, int64_t* trial,
                        int64_t* local_step, int64_t* fpt_sum, double* fpt_sq, int64_t* fpt_count,
                        void* cuda_stream);
 

@@ -100,7 +100,7 @@ def load(path: str = LIB_PATH):
     L.spin_batch_samples.argtypes = [vp, P(d), i64, P(i64)]
     L.spin_batch_destroy.argtypes = [vp]
     L.spin_single_run.argtypes = [P(spin_params), i32, P(d), P(d), vp, vp, i64, i64, i32, vp, vp, vp, vp]
-    L.spin_single_escape.argtypes = [P(spin_params), i32, P(d), P(d), P(d), vp, vp, i64, vp, vp, vp, vp, vp, vp]
+    L.spin_single_escape.argtypes = [P(spin_params), i32, P(d), P(d), P(d), vp, vp, i64, i64, vp, vp, vp, vp, vp, vp]
     L.spin_batch_last_error.argtypes = [vp]
     L.spin_batch_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:

@@ -9,14 +9,16 @@
 //                    optionally summing s_z at the end of every interval
 //                    (equilibrium averages, Fig. 4);
 //   k_single_escape  renewal form of the first-passage procedure: a replica
-//                    that crosses s_z = 0 records the passage time, restarts
-//                    from the initial state as a new trial and carries on,
-//                    so that no lane of a warp idles while the slowest trial
-//                    of the warp is still running.
+//                    that crosses s_z = 0 records the passage time and
+//                    restarts from the initial state as a new trial at the
+//                    next interval start, so that no lane of a warp idles
+//                    for long while the slowest trial of the warp runs on.
 // The energy is E = -D s_z^2 - H.s, so H_eff = H + 2 D s_z z.  Noise counter
 // of pulse k: (0, k, r, 0) for replica r in the run kernel (a one-site
 // lattice with replica index r); (0, k, r + j nrep, 0) for trial j of replica
-// r in the escape kernel, k counted from the trial's start.
+// r in the escape kernel, k counted from the trial's start.  Both kernels
+// follow the pulse schedule of the global step count, so that the pulse
+// branch is the same for all lanes of a warp.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -134,15 +136,21 @@ __global__ void __launch_bounds__(128) k_single_run(RunArgs<real> A) {
 template <typename real>
 struct EscapeArgs {
     SingleCommon<real> c;
-    long long* trial;       // per replica: index j of the running trial
-    long long* local_step;  // per replica: steps completed in the running trial
+    long long* trial;       // per replica: index j of the running (or next) trial
+    long long* local_step;  // per replica: steps done in the running trial; -1 = waiting
     long long* fpt_sum;     // per replica: sum of the passage steps of finished trials
     double* fpt_sq;         // nullable: sum of their squares
     long long* fpt_count;   // per replica: number of finished trials
     real i0, i1, i2;        // initial state of every trial
-    long long nsteps;
+    long long n0, nsteps;   // global steps completed before this launch; steps to run
 };
 
+// The pulse schedule runs on the global step count n, the same for every
+// lane of a warp, so the pulse branch never diverges; a replica that crossed
+// waits (computing on its stale state, which is discarded) until the next
+// n with n mod R == 0 and starts its next trial there, so that every trial
+// sees the schedule of a fresh run: pulse after local step R/2 of each
+// interval, pulse number counted from the trial's start.
 template <typename real, bool PREC, int ST>
 __global__ void __launch_bounds__(128) k_single_escape(EscapeArgs<real> A) {
     const SingleCommon<real>& C = A.c;
@@ -153,28 +161,33 @@ __global__ void __launch_bounds__(128) k_single_escape(EscapeArgs<real> A) {
     long long j = A.trial[r], m = A.local_step[r];
     long long fsum = 0, fcnt = 0;
     double fsq = 0.0;
-    // ph = m mod R and kq = m div R, advanced without a division per step
-    int ph = (int)(m % C.R);
-    long long kq = m / C.R;
+    int ph = (int)(A.n0 % C.R);  // global phase n mod R, advanced without a division per step
     const int half = C.R / 2;
+    // a running trial must be in phase with the global schedule; one that is
+    // not (inconsistent caller state) waits for the next interval start
+    bool running = m >= 0 && (int)(m % C.R) == ph;
+    if (!running) m = -1;
+    long long mk = running ? m / C.R : 0;  // completed intervals of the running trial
     for (long long it = 0; it < A.nsteps; ++it) {
         single_step<real, PREC, ST>(s0, s1, s2, lam, C);
-        ++m;
-        if (++ph == C.R) {
-            ph = 0;
-            ++kq;
-        }
+        if (++ph == C.R) ph = 0;
+        m += running;
+        mk += running && ph == 0;
         if (C.noise && ph == half)
-            pulse_site<real>(s0, s1, s2, C.seed, 0ULL, (uint64_t)(ph == 0 ? kq - 1 : kq),
+            pulse_site<real>(s0, s1, s2, C.seed, 0ULL, (uint64_t)(ph == 0 ? mk - 1 : mk),
                              (uint64_t)r + (uint64_t)j * (uint64_t)C.nrep, sig);
-        if (s2 < real(0)) {
+        if (running && s2 < real(0)) {
             fsum += m;
             fsq += (double)m * (double)m;
             ++fcnt;
             ++j;
+            running = false;
+            m = -1;
+        }
+        if (!running && ph == 0) {
+            running = true;
             m = 0;
-            ph = 0;
-            kq = 0;
+            mk = 0;
             s0 = A.i0;
             s1 = A.i1;
             s2 = A.i2;
@@ -305,8 +318,9 @@ cudaError_t run_t(const spin_params* p, int nrep, const double* T, const double*
 
 template <typename real>
 cudaError_t escape_t(const spin_params* p, int nrep, const double* T, const double* lambda, const double* s_init,
-                     void* s, void* scratch, long long nsteps, long long* trial, long long* local_step,
-                     long long* fpt_sum, double* fpt_sq, long long* fpt_count, cudaStream_t st) {
+                     void* s, void* scratch, long long n0, long long nsteps, long long* trial,
+                     long long* local_step, long long* fpt_sum, double* fpt_sq, long long* fpt_count,
+                     cudaStream_t st) {
     cudaError_t e = upload_scales<real>(p, nrep, T, lambda, scratch, st);
     if (e != cudaSuccess) return e;
     EscapeArgs<real> A{};
@@ -319,6 +333,7 @@ cudaError_t escape_t(const spin_params* p, int nrep, const double* T, const doub
     A.i0 = (real)s_init[0];
     A.i1 = (real)s_init[1];
     A.i2 = (real)s_init[2];
+    A.n0 = n0;
     A.nsteps = nsteps;
     return dispatch<real, EscK>(p, nrep, A, st);
 }
@@ -346,22 +361,23 @@ extern "C" int spin_single_run(const spin_params* p, int32_t nrep, const double*
 }
 
 extern "C" int spin_single_escape(const spin_params* p, int32_t nrep, const double* T, const double* lambda,
-                                  const double* s_init, void* s, void* scratch, int64_t nsteps, int64_t* trial,
+                                  const double* s_init, void* s, void* scratch, int64_t n0, int64_t nsteps,
+                                  int64_t* trial,
                                   int64_t* local_step, int64_t* fpt_sum, double* fpt_sq, int64_t* fpt_count,
                                   void* cuda_stream) {
     using namespace spin;
     const int chk = check_single(p, nrep, T, lambda, s, scratch);
     if (chk != SPIN_OK) return chk;
-    if (!s_init || nsteps < 0 || !trial || !local_step || !fpt_sum || !fpt_count) return SPIN_EINVAL;
+    if (!s_init || n0 < 0 || nsteps < 0 || !trial || !local_step || !fpt_sum || !fpt_count) return SPIN_EINVAL;
     if (!std::isfinite(s_init[0]) || !std::isfinite(s_init[1]) || !std::isfinite(s_init[2]) || !(s_init[2] >= 0.0))
         return SPIN_EINVAL;
     if (nsteps == 0) return SPIN_OK;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     const cudaError_t e =
         p->precision == 64
-            ? escape_t<double>(p, nrep, T, lambda, s_init, s, scratch, nsteps, (long long*)trial,
+            ? escape_t<double>(p, nrep, T, lambda, s_init, s, scratch, n0, nsteps, (long long*)trial,
                                (long long*)local_step, (long long*)fpt_sum, fpt_sq, (long long*)fpt_count, st)
-            : escape_t<float>(p, nrep, T, lambda, s_init, s, scratch, nsteps, (long long*)trial,
+            : escape_t<float>(p, nrep, T, lambda, s_init, s, scratch, n0, nsteps, (long long*)trial,
                               (long long*)local_step, (long long*)fpt_sum, fpt_sq, (long long*)fpt_count, st);
     return e == cudaSuccess ? SPIN_OK : SPIN_ECUDA;
 }

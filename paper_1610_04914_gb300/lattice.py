@@ -306,7 +306,8 @@ class SingleSpins:
 class EscapeReplicas:
     """Renewal first-passage runs (spin_single_escape): nrep replicas start
     at ``s_init``; every crossing of s_z = 0 ends a trial, whose length in
-    steps is summed, and restarts the replica at ``s_init``."""
+    steps is summed, and the replica restarts at ``s_init`` at the next
+    noise-interval start."""
 
     def __init__(self, p: Params, T, s_init, lam=None, device="cuda", stream=None):
         self.p = p
@@ -322,30 +323,33 @@ class EscapeReplicas:
         z = lambda dt: torch.zeros(self.nrep, dtype=dt, device=device)
         self.trial, self.local_step = z(torch.int64), z(torch.int64)
         self.fpt_sum, self.fpt_count, self.fpt_sq = z(torch.int64), z(torch.int64), z(torch.float64)
+        self.n = 0
         self.stream = stream
 
     def run(self, nsteps: int) -> "EscapeReplicas":
         lam = None if self.lam is None else _host_doubles(self.lam)
         check(B.load().spin_single_escape(ctypes.byref(self.p.c()), self.nrep, _host_doubles(self.T), lam,
                                           _host_doubles(self.s_init), self.state.data_ptr(),
-                                          self.scratch.data_ptr(), int(nsteps), self.trial.data_ptr(),
+                                          self.scratch.data_ptr(), self.n, int(nsteps), self.trial.data_ptr(),
                                           self.local_step.data_ptr(), self.fpt_sum.data_ptr(),
                                           self.fpt_sq.data_ptr(), self.fpt_count.data_ptr(),
                                           _stream_ptr(self.stream)))
+        self.n += int(nsteps)
         return self
 
     def mfpt(self, groups=None):
         """Per group of replica indices (default: all replicas) a tuple
         (mean first-passage time, its standard error, finished trials, rate),
-        times in time units.  ``rate`` = finished trials / total time run,
-        the unfinished trials included: for exponentially distributed
+        times in time units.  ``rate`` = finished trials / total time inside
+        trials, the unfinished trials included and the waits for an interval
+        start excluded: for exponentially distributed
         passage times it is the unbiased estimate of 1/MFPT even when the
         run is not much longer than one passage time."""
         torch.cuda.synchronize()
         s = self.fpt_sum.double().cpu()
         q = self.fpt_sq.cpu()
         c = self.fpt_count.double().cpu()
-        open_steps = self.local_step.double().cpu()
+        open_steps = self.local_step.clamp(min=0).double().cpu()
         dt = abs(self.p.dt)
         out = []
         for g in (groups if groups is not None else [list(range(self.nrep))]):

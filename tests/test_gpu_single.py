@@ -111,14 +111,15 @@ def test_first_passage_matches_oracle(gpu, orc):
 @pytest.mark.parametrize("prec", [64, 32])
 def test_escape_renewal_matches_oracle(gpu, orc, prec):
     """The renewal kernel: each finished trial's passage step, the trial
-    count and the state of the running trial agree with the oracle run
-    trial by trial (trial j of replica r = oracle replica r + j nrep)."""
+    count, the waiting state and the running trial agree with the oracle run
+    trial by trial (trial j of replica r = oracle replica r + j nrep, started
+    at the first global step n >= the passage with n mod R == 0)."""
     nrep, R, dt, nsteps = 8, 6, 1.0 / 6.0, 400
     T, lam = [0.35 + 0.05 * r for r in range(nrep)], [0.05 + 0.02 * r for r in range(nrep)]
     p = gpu.Params(1, 1, 1, J=0.0, D=1.0, H=(1.0, 0, 0), lam=0.0, T=0.0, dt=dt, R=R,
                    integrator=gpu.RK5_BUTCHER, seed=31, precision=prec)
     e = gpu.EscapeReplicas(p, T, S_WELL, lam=lam)
-    e.run(150).run(nsteps - 150)
+    e.run(151).run(nsteps - 151)  # a call boundary inside an interval
     torch.cuda.synchronize()
     fsum, fcnt = e.fpt_sum.cpu().numpy(), e.fpt_count.cpu().numpy()
     trial, local = e.trial.cpu().numpy(), e.local_step.cpu().numpy()
@@ -128,20 +129,25 @@ def test_escape_renewal_matches_oracle(gpu, orc, prec):
     for r in range(nrep):
         j, m, a, steps = 0, 0, init.copy(), []
         tie = False
-        for _ in range(nsteps):
-            op = _orc_one(orc, p, r + j * nrep, T[r], lam[r])
-            a, _ = orc.run(op, a, 1, n0=m)
-            m += 1
-            if abs(a[2].item()) < (1e-9 if prec == 64 else 1e-4):
-                tie = True
-            if a[2].item() < 0:
-                steps.append(m)
-                j, m, a = j + 1, 0, init.copy()
+        for n in range(1, nsteps + 1):
+            if m >= 0:
+                op = _orc_one(orc, p, r + j * nrep, T[r], lam[r])
+                a, _ = orc.run(op, a, 1, n0=m)
+                m += 1
+                if abs(a[2].item()) < (1e-9 if prec == 64 else 1e-4):
+                    tie = True
+                if a[2].item() < 0:
+                    steps.append(m)
+                    j, m = j + 1, -1
+            if m < 0 and n % R == 0:
+                m, a = 0, init.copy()
         if tie and prec == 32:
             continue  # FP32 rounding may decide a marginal crossing differently
         assert not tie
         assert fcnt[r] == len(steps) and trial[r] == j and local[r] == m, r
         assert fsum[r] == sum(steps) and fsq[r] == float(sum(x * x for x in steps))
+        if m > 0 and prec == 64:
+            assert np.max(np.abs(e.state[:, r].cpu().numpy() - a.reshape(3))) < 1e-12
         total += len(steps)
     assert total > 0
 
