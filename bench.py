@@ -39,6 +39,10 @@ SMS, FP32_LANES, MAX_SM_MHZ = 152, 128, 2070.0
 # algorithmic FP32 flops of one RK4 spin-step (FMA = 2): 4 x (stencil 23 +
 # double cross product and combination 24 + stage update 12) - 6 + renorm 9
 RK4_FLOPS_PER_SPIN_STEP = 240.0
+# algorithmic FP32 flops of one Butcher-RK5 step of a single spin in a
+# uniaxial + transverse field (FMA = 2): 12 non-zero stage couplings x 3 FMA,
+# 6 right-hand sides x 29, 5 non-zero weights x 3 FMA, renormalisation 9
+RK5_FLOPS_PER_SINGLE_STEP = 285.0
 BYTES_PER_SPIN_STEP_FP32 = 24.0
 
 
@@ -316,6 +320,49 @@ def batch_timing(sp, torch, dev, flush, stream, hbm_peak, intervals=3):
             "hbm_frac_algorithmic": BYTES_PER_SPIN_STEP_FP32 * rate / 1e9 / hbm_peak}
 
 
+def single_spin_timing(sp, torch, stream, alu_peak, blocks_per_sm=10, steps32=20000, steps64=2000):
+    """Single-spin replica throughput on the escape workload of Sec. III.B
+    (renewal first-passage runs, Butcher RK5, delta t = 1/6, Delta t = 1):
+    two full waves of 128-thread blocks at 10 resident blocks per SM, FP32
+    and FP64, one launch each timed with CUDA events on its stream after a
+    warm-up launch; the state (a few MB) is L2-resident and the kernel
+    arithmetic-bound, so no flush.  Beside it the C oracle's rate on one
+    thread for the same one-spin problem."""
+    nrep = 2 * SMS * blocks_per_sm * 128
+    out = {"workload": "uniaxial spin in a transverse field, h=1/2, D=1, lambda=0.01, T=0.1, Butcher RK5, "
+                       "dt=1/6, pulse every 6 steps, renewal first-passage runs",
+           "replicas": nrep, "unit": "replica-steps/s"}
+    for prec, steps in ((32, steps32), (64, steps64)):
+        with torch.cuda.stream(stream):
+            e = _escape_replicas(sp, nrep, prec)
+            e.stream = stream
+            e.run(200)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            e.run(steps)
+            b.record(stream)
+        torch.cuda.synchronize()
+        out[f"fp{prec}"] = nrep * steps / (a.elapsed_time(b) / 1e3)
+        out[f"fp{prec}_ms"] = a.elapsed_time(b)
+    achieved = out["fp32"] * RK5_FLOPS_PER_SINGLE_STEP / 1e12
+    out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                       "frac": achieved / alu_peak, "flops_per_replica_step": RK5_FLOPS_PER_SINGLE_STEP,
+                       "kernel": "k_single_escape<float,PREC=1,6 stages>", "traffic": None,
+                       "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}
+    import oracle
+    oracle.build()
+    w = ESCAPE
+    op = oracle.Params(1, 1, 1, J=0.0, D=w["D"], H=(2 * w["h"] * w["D"], 0.0, 0.0), lam=w["lam"], T=w["T"],
+                       dt=w["dt"], R=w["R"], integrator=oracle.RK5_BUTCHER, seed=1)
+    s = np.array([w["h"], 0.0, (1 - w["h"] ** 2) ** 0.5]).reshape(3, 1, 1, 1)
+    t0 = time.perf_counter()
+    n = 200000
+    oracle.run(op, s, n)
+    out["cpu_oracle"] = {"value": n / (time.perf_counter() - t0), "unit": "replica-steps/s", "cores": 1,
+                         "kind": "oracle", "sample": f"{n} FP64 steps of one replica (no stopping)"}
+    return out
+
+
 def kernel_timing_256(sp, torch, dev, flush, stream, hbm_peak):
     """The same fused RK4 step on a 256^3 lattice (201 MB per state copy,
     larger than L2): plain-step launch time and its HBM fraction."""
@@ -449,6 +496,7 @@ def run_ours(args, ws, rank, local):
     bat = batch_timing(sp, torch, dev, flush, stream, hbm_peak) if rank == 0 and not args.no_extra else None
     k256 = kernel_timing_256(sp, torch, dev, flush, stream, hbm_peak) if rank == 0 and not args.no_extra else None
     f64 = fp64_step_timing(sp, torch, dev, flush, stream) if rank == 0 and not args.no_extra else None
+    single = single_spin_timing(sp, torch, stream, alu_peak) if rank == 0 and not args.no_extra else None
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -494,6 +542,7 @@ def run_ours(args, ws, rank, local):
             "batched": bat,
             "roofline_256": k256,
             "fp64_step": f64,
+            "single_spin": single,
             "wall_s_timed_region": wall,
             "cpu_baseline": cpu,
         }
