@@ -334,7 +334,7 @@ def single_spin_timing(sp, torch, stream, alu_peak, blocks_per_sm=10, steps32=20
            "replicas": nrep, "unit": "replica-steps/s"}
     for prec, steps in ((32, steps32), (64, steps64)):
         with torch.cuda.stream(stream):
-            e = _escape_replicas(sp, nrep, prec)
+            e = _escape_replicas(sp, nrep, prec)   # uploads the noise scales once
             e.stream = stream
             e.run(200)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -360,6 +360,37 @@ def single_spin_timing(sp, torch, stream, alu_peak, blocks_per_sm=10, steps32=20
     oracle.run(op, s, n)
     out["cpu_oracle"] = {"value": n / (time.perf_counter() - t0), "unit": "replica-steps/s", "cores": 1,
                          "kind": "oracle", "sample": f"{n} FP64 steps of one replica (no stopping)"}
+    return out
+
+
+def noise_model_timing(sp, torch, stream, nrep=2 * SMS * 10 * 128, t_phys=200.0):
+    """GPU time per unit of physical time of the three schemes the paper
+    compares on the spin in a field (H = 1, lambda = 0.01, T = 1, FP32; Sec.
+    III.A): Heun with rectangular noise at delta t = 0.04 (noise drawn every
+    step), RK5 with rectangular noise at delta t = 0.25, pulse-noise RK5 at
+    delta t = 0.25, Delta t = 10.  One launch each, CUDA events on the stream."""
+    schemes = {"heun_rect_dt0.04": (0.04, 1, sp.HEUN, 2), "rk5_rect_dt0.25": (0.25, 1, sp.RK5_BUTCHER, 2),
+               "rk5_pulse_dt0.25_Dt10": (0.25, 40, sp.RK5_BUTCHER, 1)}
+    out = {"workload": f"spin in a field H=1, lambda=0.01, T=1, FP32, {nrep} replicas",
+           "unit": "replica time units per second"}
+    for name, (dt, R, integ, noise) in schemes.items():
+        p = sp.Params(1, 1, 1, J=0.0, D=0.0, H=(0.0, 0.0, 1.0), lam=0.01, T=1.0, dt=dt, R=R, integrator=integ,
+                      precession=1, noise=noise, seed=3, precision=32)
+        st = torch.zeros(3, nrep, dtype=torch.float64)
+        st[2] = 1.0
+        with torch.cuda.stream(stream):
+            s = sp.SingleSpins(p, [1.0] * nrep, st, stream=stream)
+            n = int(round(t_phys / dt))
+            n -= n % R
+            s.run(4 * R)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            s.run(n)
+            b.record(stream)
+        torch.cuda.synchronize()
+        out[name] = nrep * n * dt / (a.elapsed_time(b) / 1e3)
+    out["pulse_rk5_over_heun"] = out["rk5_pulse_dt0.25_Dt10"] / out["heun_rect_dt0.04"]
+    out["rect_rk5_over_heun"] = out["rk5_rect_dt0.25"] / out["heun_rect_dt0.04"]
     return out
 
 
@@ -497,6 +528,7 @@ def run_ours(args, ws, rank, local):
     k256 = kernel_timing_256(sp, torch, dev, flush, stream, hbm_peak) if rank == 0 and not args.no_extra else None
     f64 = fp64_step_timing(sp, torch, dev, flush, stream) if rank == 0 and not args.no_extra else None
     single = single_spin_timing(sp, torch, stream, alu_peak) if rank == 0 and not args.no_extra else None
+    noise_models = noise_model_timing(sp, torch, stream) if rank == 0 and not args.no_extra else None
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -543,6 +575,7 @@ def run_ours(args, ws, rank, local):
             "roofline_256": k256,
             "fp64_step": f64,
             "single_spin": single,
+            "noise_models": noise_models,
             "wall_s_timed_region": wall,
             "cpu_baseline": cpu,
         }

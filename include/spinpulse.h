@@ -66,7 +66,14 @@ typedef struct spin_params {
     int32_t precession;       /* 1: full Eq. (LLL); 0: slow equation, precession dropped (Sec. II) */
     int32_t steps_per_pulse;  /* R = Delta t / delta t >= 1 */
     int32_t renorm;           /* 1: s <- s/|s| after every step (recommended) */
-    int32_t noise;            /* 1: apply the pulses; 0: deterministic (tests) */
+    int32_t noise;            /* 1: apply the pulses; 0: deterministic (tests);
+                                 2: rectangular noise, Eq. (zeta_n): the field
+                                 zeta = sqrt(2 lambda T / Delta t) G_k added to
+                                 H_eff in the precession term of Eq. (LLL) and
+                                 held over each interval of R steps (needs
+                                 precession = 1; single-spin calls only, the
+                                 lattice and batch calls return
+                                 SPIN_EUNSUPPORTED) */
     int32_t replica;          /* replica number, third word of the noise counter */
     int32_t path;             /* 0: fused single-kernel step where the tableau allows
                                  (RK4, RK2 midpoint, Heun), else per-stage kernels;
@@ -253,28 +260,41 @@ int spin_batch_destroy(spin_batch* b);
 const char* spin_batch_last_error(const spin_batch* b);
 
 /*
- * Single-spin replicas (paper Sec. III: a spin in a field, Eq. s_evolution_anal
- * and Fig. 4; a uniaxial spin in a transverse field and its thermally
+ * Single-spin replicas (paper Sec. III: a spin in a field, Eq. s_evolution_anal,
+ * Figs. 1, 2 and 4; a uniaxial spin in a transverse field and its thermally
  * activated escape, Sec. III.B and Fig. 6).  nrep independent spins with
  * energy E = -D s_z^2 - H.s (H_eff = H + 2D s_z z; J, nx, ny, nz, replica,
- * path and bc of p are ignored), one GPU thread each, with the integrator,
- * renormalisation and pulse schedule of spin_step_pulse.  Replica r has
- * temperature T[r] and damping lambda[r] (host arrays of nrep values;
- * lambda NULL: p->lambda for all).
+ * path and bc of p are ignored), one GPU thread each, with the integrator
+ * and renormalisation of spin_step_pulse and the noise p->noise: 1 pulses
+ * (Eqs. (phi_n), (s_rotation)) after step n with n mod R == R/2, or 2
+ * rectangular noise (Eq. (zeta_n)): the field of interval k = (n-1) div R,
+ * drawn with the counter of pulse k, added to H_eff in the precession term
+ * of every stage of the interval's steps (needs p->precession = 1).
  *   s        device array of 3*nrep values of the state type: s_x of all
  *            replicas, then s_y, then s_z; updated in place
  *   scratch  device array of 2*nrep values of the state type, caller-owned,
- *            receives the pulse angle scales and dampings
- * Both calls upload those scales synchronously, then launch one kernel on
- * cuda_stream and return without waiting for it.
- * Errors: SPIN_EINVAL (bad sizes, pointers, parameters, T or lambda negative
- * or non-finite), SPIN_ECUDA.
+ *            filled by spin_single_prepare
+ * Errors: SPIN_EINVAL (bad sizes, pointers or parameters), SPIN_ECUDA.
  */
 
 /*
+ * spin_single_prepare: replica r has temperature T[r] and damping lambda[r]
+ * (host arrays of nrep values; lambda NULL: p->lambda for all).  Computes in
+ * FP64 the noise scale of each replica -- sqrt(2 lambda T Delta t) for
+ * pulses, sqrt(2 lambda T / Delta t) for rectangular noise, Delta t = R|dt|
+ * -- and copies scales and dampings into scratch, synchronously on
+ * cuda_stream.  Call again whenever T, lambda, R, dt or the noise kind
+ * change; the run and escape calls below read scratch only.
+ * Errors: SPIN_EINVAL (also T or lambda negative or non-finite).
+ */
+int spin_single_prepare(const spin_params* p, int32_t nrep, const double* T, const double* lambda,
+                        void* scratch, void* cuda_stream);
+
+/*
  * spin_single_run: advance every replica from completed step n0 by nsteps
- * steps; pulse k of replica r uses noise counter (0, k, r, 0), so replica r
- * follows exactly a one-site lattice with replica index r and J = 0.
+ * steps (one kernel launch on cuda_stream, asynchronous); the noise of
+ * replica r uses counter (0, k, r, 0), so replica r follows exactly a
+ * one-site lattice with replica index r and J = 0.
  *   stop_on_crossing  1: a replica stops after the first step that leaves
  *            s_z < 0 and stores that step number in first_passage[r]
  *            (device int64, -1 = none yet; replicas with a stored step are
@@ -283,31 +303,31 @@ const char* spin_batch_last_error(const spin_batch* b);
  *   sz_sum, sz_count  nullable device arrays (FP64, int64) accumulating s_z
  *            after every step with n mod R == 0 (equilibrium averages)
  */
-int spin_single_run(const spin_params* p, int32_t nrep, const double* T, const double* lambda, void* s,
-                    void* scratch, int64_t n0, int64_t nsteps, int32_t stop_on_crossing, int64_t* first_passage,
-                    double* sz_sum, int64_t* sz_count, void* cuda_stream);
+int spin_single_run(const spin_params* p, int32_t nrep, void* s, void* scratch, int64_t n0, int64_t nsteps,
+                    int32_t stop_on_crossing, int64_t* first_passage, double* sz_sum, int64_t* sz_count,
+                    void* cuda_stream);
 
 /*
- * spin_single_escape: renewal form of the first-passage procedure.  Every
- * replica advances nsteps steps from completed global step n0.  When a step
- * leaves s_z < 0 the replica adds the number of steps of its current trial
- * to fpt_sum[r] (and its square to fpt_sq[r], nullable), increments
- * fpt_count[r] and trial[r], sets local_step[r] = -1 and waits until the
- * next global step n with n mod R == 0 (at most R-1 steps); there it
- * restarts from s_init (host, 3 values) with local_step[r] = 0.  Every trial
- * thus starts at the beginning of a noise interval and sees the schedule of
- * a fresh run; trial j of replica r uses noise counter (0, k, r + j*nrep, 0),
- * k counted from the trial's start.  trial, local_step, fpt_sum, fpt_count:
- * device int64 arrays of nrep values.  Start: all zero, s = s_init, n0 = 0
- * (or any multiple of R); later calls pass n0 = steps completed so far.  A
- * running replica whose local_step is out of phase with n0 (local_step mod
- * R != n0 mod R) is treated as waiting.  The mean first-passage time is
+ * spin_single_escape: renewal form of the first-passage procedure (one
+ * kernel launch on cuda_stream, asynchronous).  Every replica advances
+ * nsteps steps from completed global step n0.  When a step leaves s_z < 0
+ * the replica adds the number of steps of its current trial to fpt_sum[r]
+ * (and its square to fpt_sq[r], nullable), increments fpt_count[r] and
+ * trial[r], sets local_step[r] = -1 and waits until the next global step n
+ * with n mod R == 0 (at most R-1 steps); there it restarts from s_init (host,
+ * 3 values, s_init[2] >= 0) with local_step[r] = 0.  Every trial thus starts
+ * at the beginning of a noise interval and sees the schedule of a fresh run;
+ * trial j of replica r uses noise counter (0, k, r + j*nrep, 0), k counted
+ * from the trial's start.  trial, local_step, fpt_sum, fpt_count: device
+ * int64 arrays of nrep values.  Start: all zero, s = s_init, n0 = 0 (or any
+ * multiple of R); later calls pass n0 = steps completed so far.  A running
+ * replica whose local_step is out of phase with n0 (local_step mod R !=
+ * n0 mod R) is treated as waiting.  The mean first-passage time is
  * sum(fpt_sum)/sum(fpt_count) steps.
  */
-int spin_single_escape(const spin_params* p, int32_t nrep, const double* T, const double* lambda,
-                       const double* s_init, void* s, void* scratch, int64_t n0, int64_t nsteps, int64_t* trial,
-                       int64_t* local_step, int64_t* fpt_sum, double* fpt_sq, int64_t* fpt_count,
-                       void* cuda_stream);
+int spin_single_escape(const spin_params* p, int32_t nrep, const double* s_init, void* s, void* scratch,
+                       int64_t n0, int64_t nsteps, int64_t* trial, int64_t* local_step, int64_t* fpt_sum,
+                       double* fpt_sq, int64_t* fpt_count, void* cuda_stream);
 
 /*
  * Observables of caller-owned spin arrays with no memory allocation at all.

@@ -96,6 +96,7 @@ def lib():
         L.orc_philox4x64.argtypes = [P(u64), P(u64), P(u64)]
         L.orc_gauss3.argtypes = [P(u64), P(d)]
         L.orc_noise_gauss.argtypes = [u64, i64, i64, i64, P(d)]
+        L.orc_rect_field.argtypes = [P(_Params), i64, P(d)]
         L.orc_heff.argtypes = [P(_Params), P(d), P(d), P(d)]
         L.orc_rhs.argtypes = [P(_Params), P(d), P(d), P(d)]
         L.orc_integrate.argtypes = [P(_Params), P(d), P(d)]
@@ -226,15 +227,29 @@ def observables(p: Params, s, h_site=None) -> np.ndarray:
     return out
 
 
-def run(p: Params, s, nsteps: int, n0: int = 0, h_site=None, noise: bool = True):
+NOISE_NONE, NOISE_PULSE, NOISE_RECT = 0, 1, 2
+
+
+def run(p: Params, s, nsteps: int, n0: int = 0, h_site=None, noise=True):
     """Advance nsteps from completed step n0.  Returns (state, samples) with
-    samples rows (n, M_x, M_y, M_z, E) taken after steps with n mod R == 0."""
+    samples rows (n, M_x, M_y, M_z, E) taken after steps with n mod R == 0.
+    noise: False/0 none, True/1 the pulses (Eq. (phi_n)), 2 rectangular noise
+    (Eq. (zeta_n), needs the precession term)."""
     a = _state(p, s)
     hs = _field(p, h_site)
     cap = nsteps // max(p.R, 1) + 2
     smp = np.zeros((cap, 5))
     ns = lib().orc_run(ctypes.byref(p.c()), _dp(a), _dp(hs), n0, nsteps, int(noise), _dp(smp), cap)
+    if ns < 0:
+        raise ValueError("rectangular noise needs the precession term (precession=1)")
     return a, smp[:ns]
+
+
+def rect_field(p: Params, k: int) -> np.ndarray:
+    """Rectangular-noise field of interval k at every site, shape (3, nz, ny, nx)."""
+    z = np.zeros((3, p.nz, p.ny, p.nx))
+    lib().orc_rect_field(ctypes.byref(p.c()), k, _dp(z))
+    return z
 
 
 def metropolis(p: Params, s, nsweeps: int, mc_seed: int, R_trial=None, sweep0: int = 0, h_site=None):

@@ -177,7 +177,10 @@ static void cross(const double a[3], const double b[3], double c[3])
     c[2] = a[0] * b[1] - a[1] * b[0];
 }
 
-void orc_rhs(const orc_params *p, const double *s, const double *hsite, double *f)
+/* Right-hand side of Eq. (LLL) at every site.  zeta (3N values or NULL) is
+   the rectangular-noise field of Eq. (zeta_n); it enters the precession
+   term only: f = s x (H_eff + zeta) - lambda s x (s x H_eff). */
+static void rhs_field(const orc_params *p, const double *s, const double *hsite, const double *zeta, double *f)
 {
     const int64_t N = (int64_t)p->nx * p->ny * p->nz;
     for (int z = 0; z < p->nz; ++z)
@@ -185,15 +188,22 @@ void orc_rhs(const orc_params *p, const double *s, const double *hsite, double *
             for (int x = 0; x < p->nx; ++x) {
                 int64_t i = site_index(p, x, y, z);
                 double h[3], si[3] = {s[i], s[N + i], s[2 * N + i]};
-                double sxh[3], sxsxh[3];
+                double sxh[3], sxsxh[3], hp[3], prec[3];
                 heff_site(p, s, hsite, x, y, z, h);
                 cross(si, h, sxh);
                 cross(si, sxh, sxsxh);
+                for (int a = 0; a < 3; ++a) hp[a] = h[a] + (zeta ? zeta[a * N + i] : 0.0);
+                cross(si, hp, prec);
                 for (int a = 0; a < 3; ++a) {
                     double damp = -p->lambda * sxsxh[a];
-                    f[a * N + i] = p->precession ? (sxh[a] + damp) : damp;
+                    f[a * N + i] = p->precession ? (prec[a] + damp) : damp;
                 }
             }
+}
+
+void orc_rhs(const orc_params *p, const double *s, const double *hsite, double *f)
+{
+    rhs_field(p, s, hsite, NULL, f);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -214,11 +224,14 @@ static void lincomb(int64_t len, double *y, const double *x, int n,
     }
 }
 
-/* K = h * f(x) */
+/* K = h * f(x); the rectangular-noise field (or NULL) is the same in every
+   stage of the step: the noise is held constant over its interval */
+static const double *stage_zeta = NULL;
+
 static void stage(const orc_params *p, const double *x, const double *hsite, double *K)
 {
     const int64_t len = 3LL * p->nx * p->ny * p->nz;
-    orc_rhs(p, x, hsite, K);
+    rhs_field(p, x, hsite, stage_zeta, K);
     for (int64_t q = 0; q < len; ++q) K[q] *= p->dt;
 }
 
@@ -379,18 +392,44 @@ int64_t orc_pulse_number(int64_t n, int32_t R)
     return (n - 1) / R;
 }
 
+/* Rectangular noise, Eq. (zeta_n): the field of interval k at every site,
+   zeta_i = sqrt(2 lambda T / Delta t) G_i with the same Gaussian triple that
+   pulse k would use (Delta t = R dt is the interval over which the field is
+   held). */
+void orc_rect_field(const orc_params *p, int64_t k, double *zeta)
+{
+    const int64_t N = (int64_t)p->nx * p->ny * p->nz;
+    const double scale = sqrt(2.0 * p->lambda * p->T / (p->R * fabs(p->dt)));
+    for (int64_t i = 0; i < N; ++i) {
+        double G[3];
+        orc_noise_gauss(p->seed, i, k, p->replica, G);
+        for (int a = 0; a < 3; ++a) zeta[a * N + i] = scale * G[a];
+    }
+}
+
 /* Advance from step n0 (completed) by nsteps.  Writes one record
    (n, M_x, M_y, M_z, E) per sample into samples (capacity max_samples
-   records) and returns the number written.  noise = 0 skips the pulses. */
+   records) and returns the number written.  noise = 0: no noise;
+   1: the pulses; 2: rectangular noise, the field of interval (n-1) div R in
+   the precession term of step n (returns -1 when precession is off, since
+   the noise has nowhere to enter). */
 int64_t orc_run(const orc_params *p, double *s, const double *hsite,
                 int64_t n0, int64_t nsteps, int noise,
                 double *samples, int64_t max_samples)
 {
     int64_t ns = 0;
+    double *zeta = NULL;
+    if (noise == 2) {
+        if (!p->precession) return -1;
+        zeta = malloc(sizeof(double) * 3 * (size_t)p->nx * p->ny * p->nz);
+    }
     for (int64_t n = n0 + 1; n <= n0 + nsteps; ++n) {
+        if (zeta && (n == n0 + 1 || (n - 1) % p->R == 0)) orc_rect_field(p, (n - 1) / p->R, zeta);
+        stage_zeta = zeta;
         orc_integrate(p, s, hsite);
+        stage_zeta = NULL;
         if (p->renorm) orc_renormalise(p, s);
-        if (noise && orc_is_pulse_step(n, p->R)) orc_pulse(p, s, orc_pulse_number(n, p->R));
+        if (noise == 1 && orc_is_pulse_step(n, p->R)) orc_pulse(p, s, orc_pulse_number(n, p->R));
         if (n % p->R == 0 && samples && ns < max_samples) {
             double o[4];
             orc_observables(p, s, hsite, o);
@@ -402,6 +441,7 @@ int64_t orc_run(const orc_params *p, double *s, const double *hsite,
             ++ns;
         }
     }
+    free(zeta);
     return ns;
 }
 

@@ -80,7 +80,8 @@ int bset_err(spin_batch* b, int code, const char* fmt, ...) {
 
 int validate_batch(const spin_params* p, int nrep, const int32_t* L, const double* T) {
     if (!p || nrep < 1 || !L) return SPIN_EINVAL;
-    if (p->precision != 32 || p->bc != 0) return SPIN_EUNSUPPORTED;
+    if (p->noise < 0 || p->noise > 2) return SPIN_EINVAL;
+    if (p->precision != 32 || p->bc != 0 || p->noise == 2) return SPIN_EUNSUPPORTED;
     const Tableau tb = tableau_for(p->integrator);
     if (!tb.chain || !(tb.stages == 2 || tb.stages == 4)) return SPIN_EUNSUPPORTED;
     if (p->steps_per_pulse < 1 || !std::isfinite(p->dt) || p->dt == 0.0 || !(p->lambda >= 0.0)) return SPIN_EINVAL;

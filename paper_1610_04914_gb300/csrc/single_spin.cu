@@ -2,7 +2,9 @@
 // in a transverse field with its thermally activated escape, Sec. III.B).
 // One thread owns one replica and integrates it through many steps in
 // registers, with the pulse noise of Eqs. (phi_n) and (s_rotation) once per
-// noise interval.  Two kernels:
+// noise interval, or with the rectangular noise of Eq. (zeta_n) -- a random
+// field in the precession term held over each interval, the conventional
+// scheme the paper compares with (Sec. III.A).  Two kernels:
 //   k_single_run     a fixed stretch of steps on the global step count n,
 //                    optionally stopping at the first step after which
 //                    s_z < 0 (the paper's first-passage procedure) and
@@ -36,7 +38,7 @@ struct SingleCommon {
     real* sx;
     real* sy;
     real* sz;
-    const real* sigma;   // per replica: sqrt(2 lambda_r T_r Delta t)
+    const real* sigma;   // per replica: sqrt(2 lambda_r T_r Delta t), or sqrt(2 lambda_r T_r / Delta t) (RECT)
     const real* lambda;  // per replica damping
     int nrep, R, renorm, noise;
     real D2, Hx, Hy, Hz, dt;
@@ -45,9 +47,12 @@ struct SingleCommon {
     uint64_t seed;
 };
 
-// One step of the integrator with ST stages on one spin, then |s| = 1.
-template <typename real, bool PREC, int ST>
-__device__ __forceinline__ void single_step(real& s0, real& s1, real& s2, real lam, const SingleCommon<real>& C) {
+// One step of the integrator with ST stages on one spin, then |s| = 1.  RECT:
+// the rectangular-noise field z is added to H_eff in the precession term of
+// every stage (Eqs. (LLL), (zeta_n)); otherwise the noiseless equation.
+template <typename real, bool PREC, int ST, bool RECT>
+__device__ __forceinline__ void single_step(real& s0, real& s1, real& s2, real lam, const SingleCommon<real>& C,
+                                            real z0, real z1, real z2) {
     real K[ST][3];
 #pragma unroll
     for (int j = 0; j < ST; ++j) {
@@ -60,7 +65,10 @@ __device__ __forceinline__ void single_step(real& s0, real& s1, real& s2, real l
             x2 += c * K[l][2];
         }
         real f0, f1, f2;
-        llg_rhs<real, PREC>(x0, x1, x2, C.Hx, C.Hy, C.Hz + C.D2 * x2, lam, f0, f1, f2);
+        if (RECT)
+            llg_rhs_noise<real>(x0, x1, x2, C.Hx, C.Hy, C.Hz + C.D2 * x2, z0, z1, z2, lam, f0, f1, f2);
+        else
+            llg_rhs<real, PREC>(x0, x1, x2, C.Hx, C.Hy, C.Hz + C.D2 * x2, lam, f0, f1, f2);
         K[j][0] = C.dt * f0;
         K[j][1] = C.dt * f1;
         K[j][2] = C.dt * f2;
@@ -79,6 +87,16 @@ __device__ __forceinline__ void single_step(real& s0, real& s1, real& s2, real l
     }
 }
 
+// Rectangular-noise field of interval k: zeta = zs G(seed, 0, k, replica).
+template <typename real>
+__device__ __forceinline__ void draw_zeta(const SingleCommon<real>& C, uint64_t k, uint64_t replica, real zs,
+                                          real& z0, real& z1, real& z2) {
+    Gauss<real>::draw(noise_words(C.seed, 0ULL, k, replica), z0, z1, z2);
+    z0 *= zs;
+    z1 *= zs;
+    z2 *= zs;
+}
+
 template <typename real>
 struct RunArgs {
     SingleCommon<real> c;
@@ -89,7 +107,7 @@ struct RunArgs {
     int stop;
 };
 
-template <typename real, bool PREC, int ST>
+template <typename real, bool PREC, int ST, bool RECT>
 __global__ void __launch_bounds__(128) k_single_run(RunArgs<real> A) {
     const SingleCommon<real>& C = A.c;
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -100,19 +118,22 @@ __global__ void __launch_bounds__(128) k_single_run(RunArgs<real> A) {
     const real sig = C.sigma[r], lam = C.lambda[r];
     double acc = 0.0;
     long long cnt = 0;
-    // position in the pulse schedule, advanced without a division per step:
+    // position in the schedule, advanced without a division per step:
     // ph = n mod R and kq = n div R for the step n just completed
     int ph = (int)(A.n0 % C.R);
     long long kq = A.n0 / C.R;
     const int half = C.R / 2;
+    real z0 = 0, z1 = 0, z2 = 0;
+    if (RECT && ph != 0) draw_zeta<real>(C, (uint64_t)kq, (uint64_t)r, sig, z0, z1, z2);  // mid-interval start
     for (long long n = A.n0 + 1; n <= A.n0 + A.nsteps; ++n) {
-        single_step<real, PREC, ST>(s0, s1, s2, lam, C);
+        if (RECT && ph == 0) draw_zeta<real>(C, (uint64_t)kq, (uint64_t)r, sig, z0, z1, z2);  // interval (n-1) div R
+        single_step<real, PREC, ST, RECT>(s0, s1, s2, lam, C, z0, z1, z2);
         if (++ph == C.R) {
             ph = 0;
             ++kq;
         }
         // pulse number (n - 1) div R: kq, or kq - 1 when n is a multiple of R
-        if (C.noise && ph == half)
+        if (!RECT && C.noise && ph == half)
             pulse_site<real>(s0, s1, s2, C.seed, 0ULL, (uint64_t)(ph == 0 ? kq - 1 : kq), (uint64_t)r, sig);
         if (A.sz_sum && ph == 0) {
             acc += (double)s2;
@@ -151,7 +172,7 @@ struct EscapeArgs {
 // n with n mod R == 0 and starts its next trial there, so that every trial
 // sees the schedule of a fresh run: pulse after local step R/2 of each
 // interval, pulse number counted from the trial's start.
-template <typename real, bool PREC, int ST>
+template <typename real, bool PREC, int ST, bool RECT>
 __global__ void __launch_bounds__(128) k_single_escape(EscapeArgs<real> A) {
     const SingleCommon<real>& C = A.c;
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -168,14 +189,19 @@ __global__ void __launch_bounds__(128) k_single_escape(EscapeArgs<real> A) {
     bool running = m >= 0 && (int)(m % C.R) == ph;
     if (!running) m = -1;
     long long mk = running ? m / C.R : 0;  // completed intervals of the running trial
+    const uint64_t rep0 = (uint64_t)r;
+    const uint64_t nrep = (uint64_t)C.nrep;
+    real z0 = 0, z1 = 0, z2 = 0;
+    if (RECT && ph != 0) draw_zeta<real>(C, (uint64_t)mk, rep0 + (uint64_t)j * nrep, sig, z0, z1, z2);
     for (long long it = 0; it < A.nsteps; ++it) {
-        single_step<real, PREC, ST>(s0, s1, s2, lam, C);
+        if (RECT && ph == 0) draw_zeta<real>(C, (uint64_t)mk, rep0 + (uint64_t)j * nrep, sig, z0, z1, z2);
+        single_step<real, PREC, ST, RECT>(s0, s1, s2, lam, C, z0, z1, z2);
         if (++ph == C.R) ph = 0;
         m += running;
         mk += running && ph == 0;
-        if (C.noise && ph == half)
-            pulse_site<real>(s0, s1, s2, C.seed, 0ULL, (uint64_t)(ph == 0 ? mk - 1 : mk),
-                             (uint64_t)r + (uint64_t)j * (uint64_t)C.nrep, sig);
+        if (!RECT && C.noise && ph == half)
+            pulse_site<real>(s0, s1, s2, C.seed, 0ULL, (uint64_t)(ph == 0 ? mk - 1 : mk), rep0 + (uint64_t)j * nrep,
+                             sig);
         if (running && s2 < real(0)) {
             fsum += m;
             fsq += (double)m * (double)m;
@@ -230,31 +256,35 @@ SingleCommon<real> make_common(const spin_params* p, int nrep, void* s, void* sc
     return C;
 }
 
-template <typename real, bool PREC, int ST>
+template <typename real, bool PREC, int ST, bool RECT>
 struct RunK {
     static void launch(int blocks, cudaStream_t st, const RunArgs<real>& A) {
-        k_single_run<real, PREC, ST><<<blocks, 128, 0, st>>>(A);
+        k_single_run<real, PREC, ST, RECT><<<blocks, 128, 0, st>>>(A);
     }
 };
-template <typename real, bool PREC, int ST>
+template <typename real, bool PREC, int ST, bool RECT>
 struct EscK {
     static void launch(int blocks, cudaStream_t st, const EscapeArgs<real>& A) {
-        k_single_escape<real, PREC, ST><<<blocks, 128, 0, st>>>(A);
+        k_single_escape<real, PREC, ST, RECT><<<blocks, 128, 0, st>>>(A);
     }
 };
 
-// Launch Kern<real, PREC, stages> for the integrator and precession flag.
-template <typename real, template <typename, bool, int> class Kern, typename Args>
+// Launch Kern<real, PREC, stages, RECT> for the integrator, the precession
+// flag and the noise kind (rectangular noise needs the precession term).
+template <typename real, template <typename, bool, int, bool> class Kern, typename Args>
 cudaError_t dispatch(const spin_params* p, int nrep, const Args& A, cudaStream_t st) {
     const int blocks = (nrep + 127) / 128;
     const int ns = tableau_for(p->integrator).stages;
     const bool prec = p->precession != 0;
-#define SPIN_SINGLE_CASE(NS)                                  \
-    case NS:                                                  \
-        if (prec)                                             \
-            Kern<real, true, NS>::launch(blocks, st, A);      \
-        else                                                  \
-            Kern<real, false, NS>::launch(blocks, st, A);     \
+    const bool rect = p->noise == 2;
+#define SPIN_SINGLE_CASE(NS)                                     \
+    case NS:                                                     \
+        if (rect)                                                \
+            Kern<real, true, NS, true>::launch(blocks, st, A);   \
+        else if (prec)                                           \
+            Kern<real, true, NS, false>::launch(blocks, st, A);  \
+        else                                                     \
+            Kern<real, false, NS, false>::launch(blocks, st, A); \
         break;
     switch (ns) {
         SPIN_SINGLE_CASE(2)
@@ -267,23 +297,21 @@ cudaError_t dispatch(const spin_params* p, int nrep, const Args& A, cudaStream_t
     return cudaGetLastError();
 }
 
-int check_single(const spin_params* p, int nrep, const double* T, const double* lambda, const void* s,
-                 const void* scratch) {
-    if (!p || nrep < 1 || !T || !s || !scratch) return SPIN_EINVAL;
+int check_single(const spin_params* p, int nrep, const void* s, const void* scratch) {
+    if (!p || nrep < 1 || !s || !scratch) return SPIN_EINVAL;
     if (p->precision != 32 && p->precision != 64) return SPIN_EINVAL;
     if (p->steps_per_pulse < 1 || !std::isfinite(p->dt) || p->dt == 0.0) return SPIN_EINVAL;
     if (p->integrator < 0 || p->integrator > 3) return SPIN_EINVAL;
+    if (p->noise < 0 || p->noise > 2 || (p->noise == 2 && !p->precession)) return SPIN_EINVAL;
     if (!std::isfinite(p->D) || !std::isfinite(p->H[0]) || !std::isfinite(p->H[1]) || !std::isfinite(p->H[2]))
         return SPIN_EINVAL;
-    for (int r = 0; r < nrep; ++r) {
-        const double lam = lambda ? lambda[r] : p->lambda;
-        if (!(T[r] >= 0.0) || !std::isfinite(T[r]) || !(lam >= 0.0) || !std::isfinite(lam)) return SPIN_EINVAL;
-    }
     return SPIN_OK;
 }
 
-// Upload the per-replica pulse angle scales sqrt(2 lambda_r T_r Delta t)
-// (computed in FP64) and dampings into the caller's scratch.
+// Upload the per-replica noise scales (computed in FP64) and dampings into
+// the caller's scratch: the pulse angle scale sqrt(2 lambda_r T_r Delta t),
+// Eq. (phi_n), or the rectangular field scale sqrt(2 lambda_r T_r / Delta t),
+// Eq. (zeta_n).
 template <typename real>
 cudaError_t upload_scales(const spin_params* p, int nrep, const double* T, const double* lambda, void* scratch,
                           cudaStream_t st) {
@@ -291,7 +319,7 @@ cudaError_t upload_scales(const spin_params* p, int nrep, const double* T, const
     std::vector<real> h(2 * (size_t)nrep);
     for (int r = 0; r < nrep; ++r) {
         const double lam = lambda ? lambda[r] : p->lambda;
-        h[r] = (real)std::sqrt(2.0 * lam * T[r] * Dt);
+        h[r] = (real)(p->noise == 2 ? std::sqrt(2.0 * lam * T[r] / Dt) : std::sqrt(2.0 * lam * T[r] * Dt));
         h[nrep + r] = (real)lam;
     }
     cudaError_t e = cudaMemcpyAsync(scratch, h.data(), sizeof(real) * h.size(), cudaMemcpyHostToDevice, st);
@@ -300,11 +328,8 @@ cudaError_t upload_scales(const spin_params* p, int nrep, const double* T, const
 }
 
 template <typename real>
-cudaError_t run_t(const spin_params* p, int nrep, const double* T, const double* lambda, void* s, void* scratch,
-                  long long n0, long long nsteps, int stop, long long* fp, double* sz_sum, long long* sz_count,
-                  cudaStream_t st) {
-    cudaError_t e = upload_scales<real>(p, nrep, T, lambda, scratch, st);
-    if (e != cudaSuccess) return e;
+cudaError_t run_t(const spin_params* p, int nrep, void* s, void* scratch, long long n0, long long nsteps, int stop,
+                  long long* fp, double* sz_sum, long long* sz_count, cudaStream_t st) {
     RunArgs<real> A{};
     A.c = make_common<real>(p, nrep, s, scratch);
     A.first_passage = fp;
@@ -317,12 +342,9 @@ cudaError_t run_t(const spin_params* p, int nrep, const double* T, const double*
 }
 
 template <typename real>
-cudaError_t escape_t(const spin_params* p, int nrep, const double* T, const double* lambda, const double* s_init,
-                     void* s, void* scratch, long long n0, long long nsteps, long long* trial,
-                     long long* local_step, long long* fpt_sum, double* fpt_sq, long long* fpt_count,
-                     cudaStream_t st) {
-    cudaError_t e = upload_scales<real>(p, nrep, T, lambda, scratch, st);
-    if (e != cudaSuccess) return e;
+cudaError_t escape_t(const spin_params* p, int nrep, const double* s_init, void* s, void* scratch, long long n0,
+                     long long nsteps, long long* trial, long long* local_step, long long* fpt_sum, double* fpt_sq,
+                     long long* fpt_count, cudaStream_t st) {
     EscapeArgs<real> A{};
     A.c = make_common<real>(p, nrep, s, scratch);
     A.trial = trial;
@@ -341,11 +363,28 @@ cudaError_t escape_t(const spin_params* p, int nrep, const double* T, const doub
 }  // namespace
 }  // namespace spin
 
-extern "C" int spin_single_run(const spin_params* p, int32_t nrep, const double* T, const double* lambda, void* s,
-                               void* scratch, int64_t n0, int64_t nsteps, int32_t stop_on_crossing,
-                               int64_t* first_passage, double* sz_sum, int64_t* sz_count, void* cuda_stream) {
+extern "C" int spin_single_prepare(const spin_params* p, int32_t nrep, const double* T, const double* lambda,
+                                   void* scratch, void* cuda_stream) {
     using namespace spin;
-    const int chk = check_single(p, nrep, T, lambda, s, scratch);
+    if (!p || nrep < 1 || !T || !scratch) return SPIN_EINVAL;
+    if (p->precision != 32 && p->precision != 64) return SPIN_EINVAL;
+    if (p->steps_per_pulse < 1 || !std::isfinite(p->dt) || p->dt == 0.0) return SPIN_EINVAL;
+    if (p->noise < 0 || p->noise > 2) return SPIN_EINVAL;
+    for (int r = 0; r < nrep; ++r) {
+        const double lam = lambda ? lambda[r] : p->lambda;
+        if (!(T[r] >= 0.0) || !std::isfinite(T[r]) || !(lam >= 0.0) || !std::isfinite(lam)) return SPIN_EINVAL;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const cudaError_t e = p->precision == 64 ? upload_scales<double>(p, nrep, T, lambda, scratch, st)
+                                             : upload_scales<float>(p, nrep, T, lambda, scratch, st);
+    return e == cudaSuccess ? SPIN_OK : SPIN_ECUDA;
+}
+
+extern "C" int spin_single_run(const spin_params* p, int32_t nrep, void* s, void* scratch, int64_t n0,
+                               int64_t nsteps, int32_t stop_on_crossing, int64_t* first_passage, double* sz_sum,
+                               int64_t* sz_count, void* cuda_stream) {
+    using namespace spin;
+    const int chk = check_single(p, nrep, s, scratch);
     if (chk != SPIN_OK) return chk;
     if (n0 < 0 || nsteps < 0 || (sz_sum == nullptr) != (sz_count == nullptr)) return SPIN_EINVAL;
     if (stop_on_crossing && !first_passage) return SPIN_EINVAL;
@@ -353,20 +392,18 @@ extern "C" int spin_single_run(const spin_params* p, int32_t nrep, const double*
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     const cudaError_t e =
         p->precision == 64
-            ? run_t<double>(p, nrep, T, lambda, s, scratch, n0, nsteps, stop_on_crossing,
-                            (long long*)first_passage, sz_sum, (long long*)sz_count, st)
-            : run_t<float>(p, nrep, T, lambda, s, scratch, n0, nsteps, stop_on_crossing, (long long*)first_passage,
-                           sz_sum, (long long*)sz_count, st);
+            ? run_t<double>(p, nrep, s, scratch, n0, nsteps, stop_on_crossing, (long long*)first_passage, sz_sum,
+                            (long long*)sz_count, st)
+            : run_t<float>(p, nrep, s, scratch, n0, nsteps, stop_on_crossing, (long long*)first_passage, sz_sum,
+                           (long long*)sz_count, st);
     return e == cudaSuccess ? SPIN_OK : SPIN_ECUDA;
 }
 
-extern "C" int spin_single_escape(const spin_params* p, int32_t nrep, const double* T, const double* lambda,
-                                  const double* s_init, void* s, void* scratch, int64_t n0, int64_t nsteps,
-                                  int64_t* trial,
-                                  int64_t* local_step, int64_t* fpt_sum, double* fpt_sq, int64_t* fpt_count,
-                                  void* cuda_stream) {
+extern "C" int spin_single_escape(const spin_params* p, int32_t nrep, const double* s_init, void* s, void* scratch,
+                                  int64_t n0, int64_t nsteps, int64_t* trial, int64_t* local_step, int64_t* fpt_sum,
+                                  double* fpt_sq, int64_t* fpt_count, void* cuda_stream) {
     using namespace spin;
-    const int chk = check_single(p, nrep, T, lambda, s, scratch);
+    const int chk = check_single(p, nrep, s, scratch);
     if (chk != SPIN_OK) return chk;
     if (!s_init || n0 < 0 || nsteps < 0 || !trial || !local_step || !fpt_sum || !fpt_count) return SPIN_EINVAL;
     if (!std::isfinite(s_init[0]) || !std::isfinite(s_init[1]) || !std::isfinite(s_init[2]) || !(s_init[2] >= 0.0))
@@ -375,9 +412,9 @@ extern "C" int spin_single_escape(const spin_params* p, int32_t nrep, const doub
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     const cudaError_t e =
         p->precision == 64
-            ? escape_t<double>(p, nrep, T, lambda, s_init, s, scratch, n0, nsteps, (long long*)trial,
-                               (long long*)local_step, (long long*)fpt_sum, fpt_sq, (long long*)fpt_count, st)
-            : escape_t<float>(p, nrep, T, lambda, s_init, s, scratch, n0, nsteps, (long long*)trial,
-                              (long long*)local_step, (long long*)fpt_sum, fpt_sq, (long long*)fpt_count, st);
+            ? escape_t<double>(p, nrep, s_init, s, scratch, n0, nsteps, (long long*)trial, (long long*)local_step,
+                               (long long*)fpt_sum, fpt_sq, (long long*)fpt_count, st)
+            : escape_t<float>(p, nrep, s_init, s, scratch, n0, nsteps, (long long*)trial, (long long*)local_step,
+                              (long long*)fpt_sum, fpt_sq, (long long*)fpt_count, st);
     return e == cudaSuccess ? SPIN_OK : SPIN_ECUDA;
 }

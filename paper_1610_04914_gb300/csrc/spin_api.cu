@@ -73,6 +73,8 @@ int validate(const spin_params* p) {
         if (!std::isfinite(p->H[a])) return SPIN_EINVAL;
     if (p->path < 0 || p->path > 1 || p->bc < 0 || p->bc > 1) return SPIN_EINVAL;
     if (p->replica < 0) return SPIN_EINVAL;
+    if (p->noise < 0 || p->noise > 2) return SPIN_EINVAL;
+    if (p->noise == 2) return SPIN_EUNSUPPORTED;  // rectangular noise: single-spin calls only
     return SPIN_OK;
 }
 

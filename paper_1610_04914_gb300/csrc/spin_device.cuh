@@ -151,6 +151,23 @@ __device__ __forceinline__ void pulse_site(real& sx, real& sy, real& sz, uint64_
     pulse_rotate<real>(sx, sy, sz, sigma * g0, sigma * g1, sigma * g2);
 }
 
+// Right-hand side of Eq. (LLL) with a rectangular-noise field zeta, which
+// enters the precession term only:  f = s x (H + zeta) - lambda s x (s x H).
+template <typename real>
+__device__ __forceinline__ void llg_rhs_noise(real sx, real sy, real sz, real hx, real hy, real hz, real zx,
+                                              real zy, real zz, real lambda, real& fx, real& fy, real& fz) {
+    const real cx = sy * hz - sz * hy;
+    const real cy = sz * hx - sx * hz;
+    const real cz = sx * hy - sy * hx;
+    const real bx = sy * cz - sz * cy;
+    const real by = sz * cx - sx * cz;
+    const real bz = sx * cy - sy * cx;
+    const real px = hx + zx, py = hy + zy, pz = hz + zz;
+    fx = (sy * pz - sz * py) - lambda * bx;
+    fy = (sz * px - sx * pz) - lambda * by;
+    fz = (sx * py - sy * px) - lambda * bz;
+}
+
 // Right-hand side of Eq. (LLL) without noise, given H_eff = (hx, hy, hz):
 //   a = s x H,  b = s x a
 //   precessional: f = a - lambda b;   slow (precession dropped): f = -lambda b

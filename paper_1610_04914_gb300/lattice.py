@@ -272,6 +272,14 @@ def _host_doubles(vals):
     return (ctypes.c_double * len(vals))(*vals)
 
 
+def _prepare(obj):
+    """spin_single_prepare: per-replica noise scales and dampings into the
+    object's scratch (once; the run calls are plain asynchronous launches)."""
+    lam = None if obj.lam is None else _host_doubles(obj.lam)
+    check(B.load().spin_single_prepare(ctypes.byref(obj.p.c()), obj.nrep, _host_doubles(obj.T), lam,
+                                       obj.scratch.data_ptr(), _stream_ptr(obj.stream)))
+
+
 class SingleSpins:
     """nrep independent spins with E = -D s_z^2 - H.s at temperatures T[r]
     and dampings lam[r] (default p.lam), one GPU thread each
@@ -291,10 +299,10 @@ class SingleSpins:
         self.sz_count = torch.zeros(self.nrep, dtype=torch.int64, device=device)
         self.n = 0
         self.stream = stream
+        _prepare(self)
 
     def run(self, nsteps: int, stop_on_crossing: bool = False, average: bool = False) -> "SingleSpins":
-        lam = None if self.lam is None else _host_doubles(self.lam)
-        check(B.load().spin_single_run(ctypes.byref(self.p.c()), self.nrep, _host_doubles(self.T), lam,
+        check(B.load().spin_single_run(ctypes.byref(self.p.c()), self.nrep,
                                        self.state.data_ptr(), self.scratch.data_ptr(), self.n, int(nsteps),
                                        int(stop_on_crossing), self.first_passage.data_ptr(),
                                        self.sz_sum.data_ptr() if average else None,
@@ -325,10 +333,10 @@ class EscapeReplicas:
         self.fpt_sum, self.fpt_count, self.fpt_sq = z(torch.int64), z(torch.int64), z(torch.float64)
         self.n = 0
         self.stream = stream
+        _prepare(self)
 
     def run(self, nsteps: int) -> "EscapeReplicas":
-        lam = None if self.lam is None else _host_doubles(self.lam)
-        check(B.load().spin_single_escape(ctypes.byref(self.p.c()), self.nrep, _host_doubles(self.T), lam,
+        check(B.load().spin_single_escape(ctypes.byref(self.p.c()), self.nrep,
                                           _host_doubles(self.s_init), self.state.data_ptr(),
                                           self.scratch.data_ptr(), self.n, int(nsteps), self.trial.data_ptr(),
                                           self.local_step.data_ptr(), self.fpt_sum.data_ptr(),

@@ -74,6 +74,47 @@ def test_run_matches_oracle(gpu, orc, prec, integ, precession, R, nsteps):
         assert abs(sz_sum[r] - acc) < tol * max(k, 1)
 
 
+RECT_CASES = [  # precision, integrator, R, nsteps, first call
+    (64, 1, 4, 30, 13),
+    (64, 3, 1, 40, 17),
+    (64, 0, 3, 25, 10),
+    (32, 1, 4, 24, 9),
+    (32, 3, 1, 40, 21),
+]
+
+
+@pytest.mark.parametrize("prec,integ,R,nsteps,first", RECT_CASES)
+def test_run_rectangular_noise_matches_oracle(gpu, orc, prec, integ, R, nsteps, first):
+    """Rectangular noise, Eq. (zeta_n) (noise = 2): the field of interval k
+    uses the counter of pulse k; calls that end mid-interval resume with the
+    same field."""
+    nrep = 45
+    T = np.linspace(0.1, 1.5, nrep)
+    lam = np.linspace(0.002, 0.2, nrep)
+    p = gpu.Params(1, 1, 1, J=0.0, D=0.6, H=(0.2, 0.1, 0.7), lam=0.0, T=0.0, dt=0.07, R=R, integrator=integ,
+                   precession=1, noise=2, seed=41, precision=prec)
+    s0 = _start(nrep, 6)
+    ss = gpu.SingleSpins(p, T, torch.from_numpy(s0), lam=lam)
+    ss.run(first).run(nsteps - first)
+    torch.cuda.synchronize()
+    got = ss.state.double().cpu().numpy()
+    tol = 1e-12 if prec == 64 else 2e-5
+    s0i = _input(prec, s0)
+    for r in range(nrep):
+        op = _orc_one(orc, p, r, T[r], lam[r])
+        a, _ = orc.run(op, s0i[:, r].reshape(3, 1, 1, 1), nsteps, noise=2)
+        assert np.max(np.abs(got[:, r] - a.reshape(3))) < tol, r
+
+
+def test_rectangular_noise_needs_precession(gpu):
+    p = gpu.Params(1, 1, 1, J=0.0, D=1.0, lam=0.1, T=0.3, dt=0.1, R=2, precession=0, noise=2, precision=64)
+    with pytest.raises(gpu.SpinError):
+        gpu.SingleSpins(p, [0.3], torch.tensor([[0.0], [0.0], [1.0]])).run(3)
+    q = gpu.Params(4, 4, 4, noise=2)
+    with pytest.raises(gpu.SpinError):
+        gpu.Lattice(q, torch.from_numpy(np.ascontiguousarray(_start(64, 1).reshape(3, 4, 4, 4))))
+
+
 def test_first_passage_matches_oracle(gpu, orc):
     """Stop at the first step that leaves s_z < 0 (FP64): the recorded step
     equals the oracle's, replica by replica."""
@@ -108,8 +149,8 @@ def test_first_passage_matches_oracle(gpu, orc):
     assert crossed >= nrep // 2  # at T = 0.4 most replicas cross within 100 time units
 
 
-@pytest.mark.parametrize("prec", [64, 32])
-def test_escape_renewal_matches_oracle(gpu, orc, prec):
+@pytest.mark.parametrize("prec,noise", [(64, 1), (32, 1), (64, 2)])
+def test_escape_renewal_matches_oracle(gpu, orc, prec, noise):
     """The renewal kernel: each finished trial's passage step, the trial
     count, the waiting state and the running trial agree with the oracle run
     trial by trial (trial j of replica r = oracle replica r + j nrep, started
@@ -117,7 +158,7 @@ def test_escape_renewal_matches_oracle(gpu, orc, prec):
     nrep, R, dt, nsteps = 8, 6, 1.0 / 6.0, 400
     T, lam = [0.35 + 0.05 * r for r in range(nrep)], [0.05 + 0.02 * r for r in range(nrep)]
     p = gpu.Params(1, 1, 1, J=0.0, D=1.0, H=(1.0, 0, 0), lam=0.0, T=0.0, dt=dt, R=R,
-                   integrator=gpu.RK5_BUTCHER, seed=31, precision=prec)
+                   integrator=gpu.RK5_BUTCHER, seed=31, precision=prec, noise=noise)
     e = gpu.EscapeReplicas(p, T, S_WELL, lam=lam)
     e.run(151).run(nsteps - 151)  # a call boundary inside an interval
     torch.cuda.synchronize()
@@ -132,7 +173,7 @@ def test_escape_renewal_matches_oracle(gpu, orc, prec):
         for n in range(1, nsteps + 1):
             if m >= 0:
                 op = _orc_one(orc, p, r + j * nrep, T[r], lam[r])
-                a, _ = orc.run(op, a, 1, n0=m)
+                a, _ = orc.run(op, a, 1, n0=m, noise=noise)
                 m += 1
                 if abs(a[2].item()) < (1e-9 if prec == 64 else 1e-4):
                     tie = True
@@ -178,13 +219,17 @@ def test_single_rejects_bad_arguments(gpu):
     s = torch.zeros(3, 4, dtype=torch.float64, device="cuda")
     sc = torch.zeros(8, dtype=torch.float64, device="cuda")
     T = (ctypes.c_double * 4)(0.3, 0.3, -0.1, 0.3)
-    rc = L.spin_single_run(ctypes.byref(p.c()), 4, T, None, s.data_ptr(), sc.data_ptr(), 0, 5, 0, None, None,
-                           None, None)
-    assert rc == gpu._binding.SPIN_EINVAL
+    assert L.spin_single_prepare(ctypes.byref(p.c()), 4, T, None, sc.data_ptr(), None) == B.SPIN_EINVAL
+    lam = (ctypes.c_double * 4)(0.1, float("nan"), 0.1, 0.1)
     T = (ctypes.c_double * 4)(0.3, 0.3, 0.3, 0.3)
-    rc = L.spin_single_run(ctypes.byref(p.c()), 0, T, None, s.data_ptr(), sc.data_ptr(), 0, 5, 0, None, None,
-                           None, None)
-    assert rc == gpu._binding.SPIN_EINVAL
-    rc = L.spin_single_run(ctypes.byref(p.c()), 4, T, None, s.data_ptr(), sc.data_ptr(), 0, 5, 1, None, None,
-                           None, None)
-    assert rc == gpu._binding.SPIN_EINVAL  # stop requested without a first_passage array
+    assert L.spin_single_prepare(ctypes.byref(p.c()), 4, T, lam, sc.data_ptr(), None) == B.SPIN_EINVAL
+    assert L.spin_single_prepare(ctypes.byref(p.c()), 4, T, None, sc.data_ptr(), None) == B.SPIN_OK
+    assert L.spin_single_run(ctypes.byref(p.c()), 0, s.data_ptr(), sc.data_ptr(), 0, 5, 0, None, None, None,
+                             None) == B.SPIN_EINVAL
+    # stop requested without a first_passage array
+    assert L.spin_single_run(ctypes.byref(p.c()), 4, s.data_ptr(), sc.data_ptr(), 0, 5, 1, None, None, None,
+                             None) == B.SPIN_EINVAL
+    init = (ctypes.c_double * 3)(0.0, 0.0, -1.0)  # a trial must start with s_z >= 0
+    z = torch.zeros(4, dtype=torch.int64, device="cuda")
+    assert L.spin_single_escape(ctypes.byref(p.c()), 4, init, s.data_ptr(), sc.data_ptr(), 0, 5, z.data_ptr(),
+                                z.data_ptr(), z.data_ptr(), None, z.data_ptr(), None) == B.SPIN_EINVAL
