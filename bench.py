@@ -394,6 +394,46 @@ def noise_model_timing(sp, torch, stream, nrep=2 * SMS * 10 * 128, t_phys=200.0)
     return out
 
 
+def mc_timing(sp, torch, stream, hbm_peak):
+    """The paper's speed comparison of Sec. IV on the GPU: checkerboard
+    Metropolis, 550 sweeps (the paper's match of t = 2000), against pulse
+    noise with precession dropped, delta t = 4, Delta t = 8, 500 steps
+    (t = 2000), RK2 midpoint and Butcher RK5; the paper's 64^3 free-boundary
+    particle and periodic 128^3 / 256^3 lattices, FP32, T/J = 1, ordered start.
+    CUDA events on the stream around each run."""
+    out = {"unit": "ms", "sweeps": 550, "pulse_steps": 500}
+    for n, bc in ((64, 1), (128, 0), (256, 0)):
+        s0 = spin_inputs.aligned_spins(n, n, n)
+        pm = sp.Params(n, n, n, J=1.0, T=1.0, bc=bc, precision=32)
+        with torch.cuda.stream(stream):
+            st = torch.from_numpy(s0).to("cuda", torch.float32).contiguous()
+            sp.spin_metropolis_sweeps(pm, st, 10, mc_seed=1, stream=stream)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            sp.spin_metropolis_sweeps(pm, st, 550, mc_seed=1, sweep0=10, stream=stream)
+            b.record(stream)
+        torch.cuda.synchronize()
+        mc_ms = a.elapsed_time(b)
+        row = {"mc_550_sweeps": mc_ms, "mc_trials_per_s": 550 * n ** 3 / (mc_ms / 1e3),
+               "mc_hbm_frac_algorithmic": BYTES_PER_SPIN_STEP_FP32 * 550 * n ** 3 / (mc_ms / 1e3) / 1e9 / hbm_peak}
+        for name, integ in (("pulse_rk2_500_steps", sp.RK2_MIDPOINT), ("pulse_rk5_500_steps", sp.RK5_BUTCHER)):
+            pp = sp.Params(n, n, n, J=1.0, D=0.0, H=(0.0, 0.0, 0.0), lam=0.01, T=1.0, dt=4.0, R=2,
+                           integrator=integ, precession=0, seed=17, precision=32, bc=bc)
+            with torch.cuda.stream(stream):
+                lat = sp.Lattice(pp, torch.from_numpy(s0), device="cuda:0", stream=stream)
+                lat.step(20)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                lat.step(500)
+                b.record(stream)
+            torch.cuda.synchronize()
+            row[name] = a.elapsed_time(b)
+            lat.close()
+        row["mc_over_pulse_rk2_speed"] = row["pulse_rk2_500_steps"] / mc_ms
+        out[f"{n}^3 {'free' if bc else 'periodic'}"] = row
+    return out
+
+
 def kernel_timing_256(sp, torch, dev, flush, stream, hbm_peak):
     """The same fused RK4 step on a 256^3 lattice (201 MB per state copy,
     larger than L2): plain-step launch time and its HBM fraction."""
@@ -529,6 +569,7 @@ def run_ours(args, ws, rank, local):
     f64 = fp64_step_timing(sp, torch, dev, flush, stream) if rank == 0 and not args.no_extra else None
     single = single_spin_timing(sp, torch, stream, alu_peak) if rank == 0 and not args.no_extra else None
     noise_models = noise_model_timing(sp, torch, stream) if rank == 0 and not args.no_extra else None
+    mc = mc_timing(sp, torch, stream, hbm_peak) if rank == 0 and not args.no_extra else None
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -576,6 +617,7 @@ def run_ours(args, ws, rank, local):
             "fp64_step": f64,
             "single_spin": single,
             "noise_models": noise_models,
+            "metropolis_vs_pulse": mc,
             "wall_s_timed_region": wall,
             "cpu_baseline": cpu,
         }
@@ -622,6 +664,26 @@ def run_profile_case(args):
     return 0
 
 
+def run_profile_mc(args):
+    """A small fixed case for ncu: checkerboard Metropolis on an L^3 periodic
+    FP32 ferromagnet at T/J = 1 from random spins, --profile-steps sweeps."""
+    import torch
+
+    import paper_1610_04914_gb300 as sp
+    from paper_1610_04914_gb300 import build as b
+    b.build()
+    sp.load()
+    L = args.profile_mc
+    p = sp.Params(L, L, L, J=1.0, T=1.0, precision=32)
+    st = torch.from_numpy(spin_inputs.random_spins(L, L, L, seed=1)).to("cuda", torch.float32).contiguous()
+    acc = torch.zeros(1, dtype=torch.int64, device="cuda")
+    sp.spin_metropolis_sweeps(p, st, args.profile_steps, mc_seed=1, accepted=acc)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_mc": L, "sweeps": args.profile_steps,
+                      "acceptance": int(acc.item()) / (args.profile_steps * L ** 3)}))
+    return 0
+
+
 def run_profile_single(args):
     """A small fixed case for ncu: the escape workload of Sec. III.B (h = 1/2,
     D = 1, lambda = 0.01, T = 0.1, Butcher RK5, delta t = 1/6, Delta t = 1,
@@ -653,6 +715,8 @@ def main():
     ap.add_argument("--profile-lattice", type=int, default=0,
                     help="profiling driver: L^3 FP32 RK4 lattice, --profile-steps single steps, no timing")
     ap.add_argument("--profile-steps", type=int, default=4)
+    ap.add_argument("--profile-mc", type=int, default=0,
+                    help="profiling driver: checkerboard Metropolis on an L^3 lattice, --profile-steps sweeps")
     ap.add_argument("--profile-single", type=int, default=0,
                     help="profiling driver: escape workload with this many single-spin replicas, no timing")
     args = ap.parse_args()
@@ -661,6 +725,8 @@ def main():
         return run_profile_case(args)
     if args.profile_single:
         return run_profile_single(args)
+    if args.profile_mc:
+        return run_profile_mc(args)
     if args.impl == "reference":
         return run_reference(args, ws, rank)
     return run_ours(args, ws, rank, local)

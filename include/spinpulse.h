@@ -330,6 +330,35 @@ int spin_single_escape(const spin_params* p, int32_t nrep, const double* s_init,
                        double* fpt_sq, int64_t* fpt_count, void* cuda_stream);
 
 /*
+ * Checkerboard Metropolis Monte Carlo (Sec. IV), the paper's comparison
+ * method.  nsweeps sweeps numbered sweep0, sweep0+1, ... of the lattice p
+ * (J, D, H, T, bc, replica, precision; the dynamics fields are ignored), on
+ * the caller's state s (device, SoA, 3N values of the state type, x fastest)
+ * and optional per-site field h_site (device, same layout, nullable).  Each
+ * sweep first tries every site with x+y+z even, then every site with x+y+z
+ * odd (one launch each, asynchronous on cuda_stream).  Trial at site i in
+ * sweep w: u uniform on the sphere from Philox4x64-10, counter
+ * (i, w, replica, 0), key (mc_seed, 0x6D6F6E7465 "monte"), cos(theta) =
+ * 2 u0 - 1, phi = 2 pi u1 with u = ((word >> 11) + 1/2) 2^-53;
+ * s' = (s + R_trial u)/|s + R_trial u|; accepted if dE <= 0 or
+ * u2 < exp(-dE/T), with dE the change of -s.(J sum_nn s_j + H + h_i) - D s_z^2.
+ * R_trial <= 0 selects the paper's 1.55 sqrt(T/(6J)) (needs J > 0).
+ * accepted: nullable device int64, incremented by the number of accepted
+ * trials.  Periodic lattices need even nx, ny, nz.
+ * Errors: SPIN_EINVAL, SPIN_ECUDA.
+ */
+int spin_metropolis_sweeps(const spin_params* p, void* s, const void* h_site, uint64_t mc_seed, double R_trial,
+                           int64_t sweep0, int64_t nsweeps, int64_t* accepted, void* cuda_stream);
+
+/*
+ * spin_metropolis_color: one half of sweep `sweep` -- the trials of the
+ * sites with (x+y+z) mod 2 == color (0 or 1) only, as spin_metropolis_sweeps
+ * does them; colour 0 then colour 1 of the same sweep equal one sweep.
+ */
+int spin_metropolis_color(const spin_params* p, void* s, const void* h_site, uint64_t mc_seed, double R_trial,
+                          int64_t sweep, int32_t color, int64_t* accepted, void* cuda_stream);
+
+/*
  * Observables of caller-owned spin arrays with no memory allocation at all.
  * The paper has no counterpart: this entry point serves callers that cannot
  * call cudaMalloc or ask their framework for memory where they need M and E

@@ -113,6 +113,10 @@ def lib():
         L.orc_run.restype = i64
         L.orc_metropolis.argtypes = [P(_Params), P(d), P(d), u64, d, i64, i64, P(d)]
         L.orc_metropolis.restype = i64
+        L.orc_metropolis_color.argtypes = [P(_Params), P(d), P(d), u64, d, i64, ctypes.c_int]
+        L.orc_metropolis_color.restype = i64
+        L.orc_metropolis_checkerboard.argtypes = [P(_Params), P(d), P(d), u64, d, i64, i64, P(d)]
+        L.orc_metropolis_checkerboard.restype = i64
         L.orc_rhs_vjp.argtypes = [P(_Params), P(d), P(d), P(d), P(d), P(d), P(d), P(d), P(d)]
         L.orc_step_vjp.argtypes = [P(_Params), P(d), P(d), ctypes.c_int, i64, P(d), P(d), P(d), P(d), P(d)]
         L.orc_adjoint.argtypes = [P(_Params), P(d), P(d), i64, i64, ctypes.c_int, P(d), d, P(d), P(d), P(d),
@@ -262,6 +266,33 @@ def metropolis(p: Params, s, nsweeps: int, mc_seed: int, R_trial=None, sweep0: i
     acc = lib().orc_metropolis(ctypes.byref(p.c()), _dp(a), _dp(hs), mc_seed & 0xFFFFFFFFFFFFFFFF,
                                float(R_trial), sweep0, nsweeps, _dp(ser))
     return a, ser, int(acc)
+
+
+def _trial_length(p: Params, R_trial):
+    return 1.55 * np.sqrt(p.T / (6.0 * p.J)) if R_trial is None else R_trial
+
+
+def metropolis_checkerboard(p: Params, s, nsweeps: int, mc_seed: int, R_trial=None, sweep0: int = 0,
+                            h_site=None):
+    """Checkerboard Metropolis sweeps (colour 0 = even x+y+z, then colour 1),
+    the same trials and random numbers as ``metropolis``.  Returns
+    (state, series[nsweeps,4], accepted)."""
+    a = _state(p, s)
+    hs = _field(p, h_site)
+    ser = np.zeros((nsweeps, 4))
+    acc = lib().orc_metropolis_checkerboard(ctypes.byref(p.c()), _dp(a), _dp(hs), mc_seed & 0xFFFFFFFFFFFFFFFF,
+                                            float(_trial_length(p, R_trial)), sweep0, nsweeps, _dp(ser))
+    return a, ser, int(acc)
+
+
+def metropolis_color(p: Params, s, sweep: int, color: int, mc_seed: int, R_trial=None, h_site=None):
+    """One half of checkerboard sweep ``sweep``: the sites of one colour.
+    Returns (state, accepted)."""
+    a = _state(p, s)
+    hs = _field(p, h_site)
+    acc = lib().orc_metropolis_color(ctypes.byref(p.c()), _dp(a), _dp(hs), mc_seed & 0xFFFFFFFFFFFFFFFF,
+                                     float(_trial_length(p, R_trial)), sweep, color)
+    return a, int(acc)
 
 
 # ---------------------------------------------------------------- adjoint

@@ -453,60 +453,101 @@ int64_t orc_run(const orc_params *p, double *s, const double *hsite,
 /* Pinned by the Langevin function for independent spins.                    */
 /* ------------------------------------------------------------------------ */
 
+/* One Metropolis trial at site (x, y, z) in sweep sw; returns 1 if the
+   trial was accepted (the spin then holds the trial direction). */
+static int metro_site(const orc_params *p, double *s, const double *hsite, int x, int y, int z,
+                      uint64_t mc_seed, double Rtrial, int64_t sw)
+{
+    const int64_t N = (int64_t)p->nx * p->ny * p->nz;
+    const double two_pi = 6.283185307179586476925286766559;
+    int64_t i = site_index(p, x, y, z);
+    uint64_t ctr[4] = {(uint64_t)i, (uint64_t)sw, (uint64_t)p->replica, 0};
+    uint64_t key[2] = {mc_seed, ORC_STREAM_MC}, w[4];
+    orc_philox4x64(ctr, key, w);
+    double cz = 2.0 * u01(w[0]) - 1.0, ph = two_pi * u01(w[1]);
+    double sz = sqrt(1.0 - cz * cz);
+    double u[3] = {sz * cos(ph), sz * sin(ph), cz};
+    double so[3] = {s[i], s[N + i], s[2 * N + i]}, sn[3];
+    for (int a = 0; a < 3; ++a) sn[a] = so[a] + Rtrial * u[a];
+    double nn = sqrt(sn[0] * sn[0] + sn[1] * sn[1] + sn[2] * sn[2]);
+    for (int a = 0; a < 3; ++a) sn[a] /= nn;
+    /* energy of site i with everything else fixed:
+       -s_i.(J sum_nn s_j + H + h_i) - D s_iz^2 */
+    double loc[3];
+    const int64_t nb[6] = {
+        site_index(p, x - 1, y, z), site_index(p, x + 1, y, z),
+        site_index(p, x, y - 1, z), site_index(p, x, y + 1, z),
+        site_index(p, x, y, z - 1), site_index(p, x, y, z + 1),
+    };
+    for (int a = 0; a < 3; ++a) {
+        double sum = 0.0;
+        for (int j = 0; j < 6; ++j) {
+            /* a site that neighbours itself (lattice size 1)
+               moves together with the trial spin */
+            if (nb[j] == i || nb[j] < 0) continue;
+            sum += s[a * N + nb[j]];
+        }
+        loc[a] = p->J * sum + p->H[a] + (hsite ? hsite[a * N + i] : 0.0);
+    }
+    double e_old = -(so[0] * loc[0] + so[1] * loc[1] + so[2] * loc[2]) - p->D * so[2] * so[2];
+    double e_new = -(sn[0] * loc[0] + sn[1] * loc[1] + sn[2] * loc[2]) - p->D * sn[2] * sn[2];
+    double dE = e_new - e_old;
+    int accept = dE <= 0.0 || u01(w[2]) < exp(-dE / p->T);
+    if (accept) {
+        s[i] = sn[0]; s[N + i] = sn[1]; s[2 * N + i] = sn[2];
+    }
+    return accept;
+}
+
+static void record_series(const orc_params *p, const double *s, const double *hsite, double *row)
+{
+    double o[4];
+    orc_observables(p, s, hsite, o);
+    for (int a = 0; a < 4; ++a) row[a] = o[a];
+}
+
 int64_t orc_metropolis(const orc_params *p, double *s, const double *hsite,
                        uint64_t mc_seed, double Rtrial, int64_t sweep0, int64_t nsweeps,
                        double *series)
 {
-    const int64_t N = (int64_t)p->nx * p->ny * p->nz;
-    const double two_pi = 6.283185307179586476925286766559;
     int64_t accepted = 0;
     for (int64_t sw = sweep0; sw < sweep0 + nsweeps; ++sw) {
         for (int z = 0; z < p->nz; ++z)
             for (int y = 0; y < p->ny; ++y)
-                for (int x = 0; x < p->nx; ++x) {
-                    int64_t i = site_index(p, x, y, z);
-                    uint64_t ctr[4] = {(uint64_t)i, (uint64_t)sw, (uint64_t)p->replica, 0};
-                    uint64_t key[2] = {mc_seed, ORC_STREAM_MC}, w[4];
-                    orc_philox4x64(ctr, key, w);
-                    double cz = 2.0 * u01(w[0]) - 1.0, ph = two_pi * u01(w[1]);
-                    double sz = sqrt(1.0 - cz * cz);
-                    double u[3] = {sz * cos(ph), sz * sin(ph), cz};
-                    double so[3] = {s[i], s[N + i], s[2 * N + i]}, sn[3];
-                    for (int a = 0; a < 3; ++a) sn[a] = so[a] + Rtrial * u[a];
-                    double nn = sqrt(sn[0] * sn[0] + sn[1] * sn[1] + sn[2] * sn[2]);
-                    for (int a = 0; a < 3; ++a) sn[a] /= nn;
-                    /* energy of site i with everything else fixed:
-                       -s_i.(J sum_nn s_j + H + h_i) - D s_iz^2 */
-                    double loc[3];
-                    const int64_t nb[6] = {
-                        site_index(p, x - 1, y, z), site_index(p, x + 1, y, z),
-                        site_index(p, x, y - 1, z), site_index(p, x, y + 1, z),
-                        site_index(p, x, y, z - 1), site_index(p, x, y, z + 1),
-                    };
-                    for (int a = 0; a < 3; ++a) {
-                        double sum = 0.0;
-                        for (int j = 0; j < 6; ++j) {
-                            /* a site that neighbours itself (lattice size 1)
-                               moves together with the trial spin */
-                            if (nb[j] == i || nb[j] < 0) continue;
-                            sum += s[a * N + nb[j]];
-                        }
-                        loc[a] = p->J * sum + p->H[a] + (hsite ? hsite[a * N + i] : 0.0);
-                    }
-                    double e_old = -(so[0] * loc[0] + so[1] * loc[1] + so[2] * loc[2]) - p->D * so[2] * so[2];
-                    double e_new = -(sn[0] * loc[0] + sn[1] * loc[1] + sn[2] * loc[2]) - p->D * sn[2] * sn[2];
-                    double dE = e_new - e_old;
-                    int accept = dE <= 0.0 || u01(w[2]) < exp(-dE / p->T);
-                    if (accept) {
-                        s[i] = sn[0]; s[N + i] = sn[1]; s[2 * N + i] = sn[2];
-                        ++accepted;
-                    }
-                }
-        if (series) {
-            double o[4];
-            orc_observables(p, s, hsite, o);
-            for (int a = 0; a < 4; ++a) series[4 * (sw - sweep0) + a] = o[a];
-        }
+                for (int x = 0; x < p->nx; ++x)
+                    accepted += metro_site(p, s, hsite, x, y, z, mc_seed, Rtrial, sw);
+        if (series) record_series(p, s, hsite, series + 4 * (sw - sweep0));
+    }
+    return accepted;
+}
+
+/* Checkerboard order: in sweep sw first every site with (x + y + z) even,
+   then every site with (x + y + z) odd, each half in site order.  The two
+   halves are independent sets (no two sites of one colour are neighbours)
+   when every periodic dimension is even; the random numbers of a site are
+   those of the sequential sweep, so only the order differs.
+   orc_metropolis_color does one half (colour 0 or 1) of sweep sw. */
+int64_t orc_metropolis_color(const orc_params *p, double *s, const double *hsite,
+                             uint64_t mc_seed, double Rtrial, int64_t sw, int color)
+{
+    int64_t accepted = 0;
+    for (int z = 0; z < p->nz; ++z)
+        for (int y = 0; y < p->ny; ++y)
+            for (int x = 0; x < p->nx; ++x)
+                if (((x + y + z) & 1) == color)
+                    accepted += metro_site(p, s, hsite, x, y, z, mc_seed, Rtrial, sw);
+    return accepted;
+}
+
+int64_t orc_metropolis_checkerboard(const orc_params *p, double *s, const double *hsite,
+                                    uint64_t mc_seed, double Rtrial, int64_t sweep0, int64_t nsweeps,
+                                    double *series)
+{
+    int64_t accepted = 0;
+    for (int64_t sw = sweep0; sw < sweep0 + nsweeps; ++sw) {
+        accepted += orc_metropolis_color(p, s, hsite, mc_seed, Rtrial, sw, 0);
+        accepted += orc_metropolis_color(p, s, hsite, mc_seed, Rtrial, sw, 1);
+        if (series) record_series(p, s, hsite, series + 4 * (sw - sweep0));
     }
     return accepted;
 }

@@ -11,6 +11,7 @@ from ._binding import (HEUN, RK2_MIDPOINT, RK4, RK5_BUTCHER, SPIN_ENONFINITE, SP
 from .lattice import (EscapeReplicas, Lattice, Params, SingleSpins, SpinRunFn, spin_backward, spin_backward_workspace_size,  # noqa: F401
                       spin_get_step, spin_lattice_create, spin_record_begin, spin_record_end,
                       spin_record_store_size,
-                      spin_lattice_destroy, spin_noise_draw, spin_observables, spin_observables_noalloc, spin_samples,
+                      spin_lattice_destroy, spin_metropolis_color, spin_metropolis_sweeps, spin_noise_draw, spin_observables,
+                      spin_observables_noalloc, spin_samples,
                       spin_set_step, spin_step_pulse, spin_workspace_size)
 from .batch import Batch, spin_batch_offsets, spin_batch_workspace_size  # noqa: F401,E402

@@ -54,7 +54,7 @@ EXPORTS = [
     "spin_record_begin", "spin_record_end", "spin_backward_workspace_size", "spin_backward",
     "spin_batch_offsets", "spin_batch_workspace_size", "spin_batch_create", "spin_batch_tuning",
     "spin_batch_step_pulse", "spin_batch_observables", "spin_batch_samples", "spin_batch_destroy",
-    "spin_batch_last_error", "spin_single_prepare", "spin_single_run", "spin_single_escape",
+    "spin_batch_last_error", "spin_single_prepare", "spin_single_run", "spin_single_escape", "spin_metropolis_sweeps", "spin_metropolis_color",
 ]
 
 _lib = None
@@ -99,6 +99,8 @@ def load(path: str = LIB_PATH):
     L.spin_batch_observables.argtypes = [vp, P(d)]
     L.spin_batch_samples.argtypes = [vp, P(d), i64, P(i64)]
     L.spin_batch_destroy.argtypes = [vp]
+    L.spin_metropolis_sweeps.argtypes = [P(spin_params), vp, vp, u64, d, i64, i64, vp, vp]
+    L.spin_metropolis_color.argtypes = [P(spin_params), vp, vp, u64, d, i64, i32, vp, vp]
     L.spin_single_prepare.argtypes = [P(spin_params), i32, P(d), P(d), vp, vp]
     L.spin_single_run.argtypes = [P(spin_params), i32, vp, vp, i64, i64, i32, vp, vp, vp, vp]
     L.spin_single_escape.argtypes = [P(spin_params), i32, P(d), vp, vp, i64, i64, vp, vp, vp, vp, vp, vp]

@@ -371,3 +371,34 @@ class EscapeReplicas:
             var = max(float(q[idx].sum()) / n - m * m, 0.0)
             out.append((m * dt, (var / n) ** 0.5 * dt, int(n), n / total))
         return out if groups is not None else out[0]
+
+
+def _mc_check(p, state, h_site):
+    if not (state.is_cuda and state.dtype == p.dtype and state.is_contiguous()):
+        raise ValueError("state must be a contiguous CUDA tensor of the lattice precision")
+    if h_site is not None and not (h_site.is_cuda and h_site.dtype == p.dtype and h_site.is_contiguous()):
+        raise ValueError("h_site must be a contiguous CUDA tensor of the lattice precision")
+
+
+def spin_metropolis_sweeps(p: Params, state, nsweeps: int, mc_seed: int, R_trial=None, sweep0: int = 0,
+                           h_site=None, accepted=None, stream=None) -> None:
+    """Checkerboard Metropolis sweeps on a device state tensor (3, nz, ny, nx)
+    of p's precision, in place; ``accepted`` an optional device int64 tensor
+    of one element that counts accepted trials."""
+    _mc_check(p, state, h_site)
+    check(B.load().spin_metropolis_sweeps(ctypes.byref(p.c()), state.data_ptr(),
+                                          None if h_site is None else h_site.data_ptr(),
+                                          mc_seed & 0xFFFFFFFFFFFFFFFF, -1.0 if R_trial is None else float(R_trial),
+                                          int(sweep0), int(nsweeps),
+                                          None if accepted is None else accepted.data_ptr(), _stream_ptr(stream)))
+
+
+def spin_metropolis_color(p: Params, state, sweep: int, color: int, mc_seed: int, R_trial=None, h_site=None,
+                          accepted=None, stream=None) -> None:
+    """One colour (0: x+y+z even, 1: odd) of checkerboard sweep ``sweep``."""
+    _mc_check(p, state, h_site)
+    check(B.load().spin_metropolis_color(ctypes.byref(p.c()), state.data_ptr(),
+                                         None if h_site is None else h_site.data_ptr(),
+                                         mc_seed & 0xFFFFFFFFFFFFFFFF, -1.0 if R_trial is None else float(R_trial),
+                                         int(sweep), int(color),
+                                         None if accepted is None else accepted.data_ptr(), _stream_ptr(stream)))
