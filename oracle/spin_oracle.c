@@ -224,14 +224,12 @@ static void lincomb(int64_t len, double *y, const double *x, int n,
     }
 }
 
-/* K = h * f(x); the rectangular-noise field (or NULL) is the same in every
-   stage of the step: the noise is held constant over its interval */
-static const double *stage_zeta = NULL;
-
-static void stage(const orc_params *p, const double *x, const double *hsite, double *K)
+/* K = h * f(x); zeta is the rectangular-noise field (or NULL), the same in
+   every stage of the step: the noise is held constant over its interval */
+static void stage(const orc_params *p, const double *x, const double *hsite, const double *zeta, double *K)
 {
     const int64_t len = 3LL * p->nx * p->ny * p->nz;
-    rhs_field(p, x, hsite, stage_zeta, K);
+    rhs_field(p, x, hsite, zeta, K);
     for (int64_t q = 0; q < len; ++q) K[q] *= p->dt;
 }
 
@@ -244,7 +242,7 @@ void orc_renormalise(const orc_params *p, double *s)
     }
 }
 
-void orc_integrate(const orc_params *p, double *s, const double *hsite)
+static void integrate_field(const orc_params *p, double *s, const double *hsite, const double *zeta)
 {
     const int64_t len = 3LL * p->nx * p->ny * p->nz;
     double *K[6], *xt = malloc(sizeof(double) * len);
@@ -254,10 +252,10 @@ void orc_integrate(const orc_params *p, double *s, const double *hsite)
         /* K1 = h f(x); K2 = h f(x + K1/2); K3 = h f(x + K2/2); K4 = h f(x + K3);
            x <- x + (K1 + 2 K2 + 2 K3 + K4)/6 */
         double c2[1] = {0.5}, c3[1] = {0.5}, c4[1] = {1.0};
-        stage(p, s, hsite, K[0]);
-        lincomb(len, xt, s, 1, c2, &K[0]); stage(p, xt, hsite, K[1]);
-        lincomb(len, xt, s, 1, c3, &K[1]); stage(p, xt, hsite, K[2]);
-        lincomb(len, xt, s, 1, c4, &K[2]); stage(p, xt, hsite, K[3]);
+        stage(p, s, hsite, zeta, K[0]);
+        lincomb(len, xt, s, 1, c2, &K[0]); stage(p, xt, hsite, zeta, K[1]);
+        lincomb(len, xt, s, 1, c3, &K[1]); stage(p, xt, hsite, zeta, K[2]);
+        lincomb(len, xt, s, 1, c4, &K[2]); stage(p, xt, hsite, zeta, K[3]);
         double b[4] = {1.0 / 6.0, 2.0 / 6.0, 2.0 / 6.0, 1.0 / 6.0};
         lincomb(len, s, s, 4, b, K);
     } else if (p->integrator == ORC_RK5_BUTCHER) {
@@ -266,36 +264,42 @@ void orc_integrate(const orc_params *p, double *s, const double *hsite)
            K5 = h f(x + 3(K1 + 3K4)/16);
            K6 = h f(x + (-3K1 + 2K2 + 12(K3-K4) + 8K5)/7);
            x <- x + (7K1 + 32K3 + 12K4 + 32K5 + 7K6)/90 */
-        stage(p, s, hsite, K[0]);
+        stage(p, s, hsite, zeta, K[0]);
         { double c[1] = {0.25}; lincomb(len, xt, s, 1, c, K); }
-        stage(p, xt, hsite, K[1]);
+        stage(p, xt, hsite, zeta, K[1]);
         { double c[2] = {0.125, 0.125}; lincomb(len, xt, s, 2, c, K); }
-        stage(p, xt, hsite, K[2]);
+        stage(p, xt, hsite, zeta, K[2]);
         { double c[3] = {0.0, -0.5, 1.0}; lincomb(len, xt, s, 3, c, K); }
-        stage(p, xt, hsite, K[3]);
+        stage(p, xt, hsite, zeta, K[3]);
         { double c[4] = {3.0 / 16.0, 0.0, 0.0, 9.0 / 16.0}; lincomb(len, xt, s, 4, c, K); }
-        stage(p, xt, hsite, K[4]);
+        stage(p, xt, hsite, zeta, K[4]);
         { double c[5] = {-3.0 / 7.0, 2.0 / 7.0, 12.0 / 7.0, -12.0 / 7.0, 8.0 / 7.0};
           lincomb(len, xt, s, 5, c, K); }
-        stage(p, xt, hsite, K[5]);
+        stage(p, xt, hsite, zeta, K[5]);
         double b[6] = {7.0 / 90.0, 0.0, 32.0 / 90.0, 12.0 / 90.0, 32.0 / 90.0, 7.0 / 90.0};
         lincomb(len, s, s, 6, b, K);
     } else if (p->integrator == ORC_RK2_MIDPOINT) {
         /* K1 = h f(x); K2 = h f(x + K1/2); x <- x + K2 */
         double c[1] = {0.5};
-        stage(p, s, hsite, K[0]);
-        lincomb(len, xt, s, 1, c, K); stage(p, xt, hsite, K[1]);
+        stage(p, s, hsite, zeta, K[0]);
+        lincomb(len, xt, s, 1, c, K); stage(p, xt, hsite, zeta, K[1]);
         double b[2] = {0.0, 1.0};
         lincomb(len, s, s, 2, b, K);
     } else { /* ORC_HEUN: K1 = h f(x); K2 = h f(x + K1); x <- x + (K1 + K2)/2 */
         double c[1] = {1.0};
-        stage(p, s, hsite, K[0]);
-        lincomb(len, xt, s, 1, c, K); stage(p, xt, hsite, K[1]);
+        stage(p, s, hsite, zeta, K[0]);
+        lincomb(len, xt, s, 1, c, K); stage(p, xt, hsite, zeta, K[1]);
         double b[2] = {0.5, 0.5};
         lincomb(len, s, s, 2, b, K);
     }
     for (int j = 0; j < 6; ++j) free(K[j]);
     free(xt);
+}
+
+/* One step of the noiseless equation. */
+void orc_integrate(const orc_params *p, double *s, const double *hsite)
+{
+    integrate_field(p, s, hsite, NULL);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -425,9 +429,7 @@ int64_t orc_run(const orc_params *p, double *s, const double *hsite,
     }
     for (int64_t n = n0 + 1; n <= n0 + nsteps; ++n) {
         if (zeta && (n == n0 + 1 || (n - 1) % p->R == 0)) orc_rect_field(p, (n - 1) / p->R, zeta);
-        stage_zeta = zeta;
-        orc_integrate(p, s, hsite);
-        stage_zeta = NULL;
+        integrate_field(p, s, hsite, zeta);
         if (p->renorm) orc_renormalise(p, s);
         if (noise == 1 && orc_is_pulse_step(n, p->R)) orc_pulse(p, s, orc_pulse_number(n, p->R));
         if (n % p->R == 0 && samples && ns < max_samples) {
@@ -686,7 +688,7 @@ void orc_step_vjp(const orc_params *p, const double *s, const double *hsite, int
             for (int l = 0; l < j; ++l) acc += A[j][l] * K[l][q];
             X[j][q] = acc;
         }
-        stage(p, X[j], hsite, K[j]);
+        stage(p, X[j], hsite, NULL, K[j]);
     }
     for (int64_t q = 0; q < len; ++q) {
         double acc = s[q];
