@@ -684,6 +684,40 @@ def run_profile_mc(args):
     return 0
 
 
+def run_profile_adjoint(args):
+    """A fixed case for ncu launch lists: the 64^3 differentiation workload
+    (FP32 RK4, pulse every 10, h_i, checkpoint every 50), --profile-steps
+    recorded forward steps, then the checkpointed adjoint; prints the
+    wall-clock split."""
+    import torch
+
+    import paper_1610_04914_gb300 as sp
+    from paper_1610_04914_gb300 import build as b
+    b.build()
+    sp.load()
+    w = spin_inputs.WORKLOADS["adjoint64"]
+    nx, ny, nz = w["n"]
+    p = sp.Params(nx, ny, nz, J=w["J"], D=w["D"], H=w["H"], lam=w["lam"], T=w["T"], dt=w["dt"], R=w["R"],
+                  seed=w["noise_seed"], precision=32)
+    lat = sp.Lattice(p, torch.from_numpy(spin_inputs.random_spins(nx, ny, nz, seed=w["spin_seed"])),
+                     h_site=torch.from_numpy(spin_inputs.site_fields(nx, ny, nz, w["field_sigma"],
+                                                                     seed=w["noise_seed"])))
+    n = args.profile_steps
+    lat.record(w["checkpoint"], n)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lat.step(n)
+    M, E = lat.observables()
+    t1 = time.perf_counter()
+    g = lat.backward([2.0 * (M[a] - w["m_target"][a]) for a in range(3)], 1.0, field_grad=True)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    print(json.dumps({"profile_adjoint": n, "fwd_ms_per_step": 1e3 * (t1 - t0) / n,
+                      "adjoint_ms_per_step": 1e3 * (t2 - t1) / n, "gJ": g["J"]}))
+    lat.close()
+    return 0
+
+
 def run_profile_single(args):
     """A small fixed case for ncu: the escape workload of Sec. III.B (h = 1/2,
     D = 1, lambda = 0.01, T = 0.1, Butcher RK5, delta t = 1/6, Delta t = 1,
@@ -715,6 +749,8 @@ def main():
     ap.add_argument("--profile-lattice", type=int, default=0,
                     help="profiling driver: L^3 FP32 RK4 lattice, --profile-steps single steps, no timing")
     ap.add_argument("--profile-steps", type=int, default=4)
+    ap.add_argument("--profile-adjoint", action="store_true",
+                    help="profiling driver: 64^3 adjoint workload with --profile-steps steps")
     ap.add_argument("--profile-mc", type=int, default=0,
                     help="profiling driver: checkerboard Metropolis on an L^3 lattice, --profile-steps sweeps")
     ap.add_argument("--profile-single", type=int, default=0,
@@ -727,6 +763,8 @@ def main():
         return run_profile_single(args)
     if args.profile_mc:
         return run_profile_mc(args)
+    if args.profile_adjoint:
+        return run_profile_adjoint(args)
     if args.impl == "reference":
         return run_reference(args, ws, rank)
     return run_ours(args, ws, rank, local)

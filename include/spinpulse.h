@@ -193,8 +193,10 @@ int spin_record_end(spin_lattice* h);
  *                dependence of E(s_n) on the parameters
  *   g_h_site     nullable device FP64 array of 3N: dL/dh_i (component-major)
  *   g_s0         nullable device array of 3N (state type): dL/ds_{n0}
- * Parameter gradients accumulate in FP64; the adjoint state is kept in the
- * state precision.  Synchronises the stream.
+ * Parameter gradients accumulate in FP64 over sites, stages and steps; the
+ * terms of one warp (32 sites) and, for dL/dh_i, the stage terms of one
+ * checkpoint segment are first summed in the state precision.  The adjoint
+ * state is kept in the state precision.  Synchronises the stream.
  * Errors: SPIN_EINVAL (no recording, range mismatch), SPIN_ENOSPACE, SPIN_ECUDA.
  */
 int spin_backward_workspace_size(const spin_params* p, int32_t K, size_t* bytes);

@@ -3,7 +3,9 @@
 // the forward run stores the state every K steps; the backward pass restores
 // each checkpoint, recomputes its K states with the forward kernels, and runs
 // the transposed step backwards through them.  Parameter gradients (J, D, H,
-// per-site h_i) accumulate in FP64.
+// per-site h_i) accumulate in FP64 across sites, stages and steps; partial
+// sums of 32 sites (J, D, H) and of one checkpoint segment (h_i) are formed in
+// the state precision first.
 //
 // Transposes used (f the right-hand side of Eq. LLL at fixed noise, a = s x H):
 //   w_i = (df_i/dH_i)^T v_i = -(s x v) - lambda s x (s x v)    [slow: without -(s x v)]
@@ -27,47 +29,31 @@ namespace {
 
 constexpr int kAT = 256;
 
-__device__ __forceinline__ int wrapa(int v, int n) {
-    int r = v % n;
-    return r < 0 ? r + n : r;
-}
-
-__device__ __forceinline__ void site_xyz(long long i, int nx, int ny, int& x, int& y, int& z) {
-    const int ii = (int)i;   // N < 2^31
-    x = ii % nx;
-    const int r = ii / nx;
-    y = r % ny;
-    z = r / ny;
-}
-
-// Neighbour indices x-1, x+1, y-1, y+1, z-1, z+1 (periodic), and in w the
-// weight of each: 0 for a neighbour across a face of a free-boundary lattice.
+// Neighbour indices x-1, x+1, y-1, y+1, z-1, z+1 (periodic wrap) of site i,
+// and in w the weight of each: 0 for a neighbour across a face of a
+// free-boundary lattice.  Two integer divisions per site, the wrap by
+// comparison.
 template <typename real>
-__device__ __forceinline__ void neighbour_weights(long long i, int nx, int ny, int nz, int bc, real w[6]) {
-    int x, y, z;
-    const int ii = (int)i;
-    x = ii % nx;
-    y = (ii / nx) % ny;
-    z = (ii / nx) / ny;
+__device__ __forceinline__ void neighbours_w(long long i, int nx, int ny, int nz, int bc, long long nb[6], real w[6]) {
+    const int ii = (int)i;   // N < 2^31
+    const int r = ii / nx;
+    const int x = ii - r * nx;
+    const int z = r / ny;
+    const int y = r - z * ny;
+    const long long P = (long long)nx * ny;
+    const long long N = P * nz;
+    nb[0] = x > 0 ? i - 1 : i + (nx - 1);
+    nb[1] = x < nx - 1 ? i + 1 : i - (nx - 1);
+    nb[2] = y > 0 ? i - nx : i + (long long)(ny - 1) * nx;
+    nb[3] = y < ny - 1 ? i + nx : i - (long long)(ny - 1) * nx;
+    nb[4] = z > 0 ? i - P : i + (N - P);
+    nb[5] = z < nz - 1 ? i + P : i - (N - P);
     w[0] = (bc && x == 0) ? real(0) : real(1);
     w[1] = (bc && x == nx - 1) ? real(0) : real(1);
     w[2] = (bc && y == 0) ? real(0) : real(1);
     w[3] = (bc && y == ny - 1) ? real(0) : real(1);
     w[4] = (bc && z == 0) ? real(0) : real(1);
     w[5] = (bc && z == nz - 1) ? real(0) : real(1);
-}
-
-__device__ __forceinline__ void neighbours(long long i, int nx, int ny, int nz, long long nb[6]) {
-    int x, y, z;
-    site_xyz(i, nx, ny, x, y, z);
-    const long long P = (long long)nx * ny;
-    const long long row = (long long)z * P + (long long)y * nx;
-    nb[0] = row + wrapa(x - 1, nx);
-    nb[1] = row + wrapa(x + 1, nx);
-    nb[2] = (long long)z * P + (long long)wrapa(y - 1, ny) * nx + x;
-    nb[3] = (long long)z * P + (long long)wrapa(y + 1, ny) * nx + x;
-    nb[4] = (long long)wrapa(z - 1, nz) * P + (long long)y * nx + x;
-    nb[5] = (long long)wrapa(z + 1, nz) * P + (long long)y * nx + x;
 }
 
 __device__ __forceinline__ void cross3(const double a[3], const double b[3], double c[3]) {
@@ -114,16 +100,20 @@ __device__ __forceinline__ void heff_at(const real* __restrict__ x, const real* 
 }
 
 // K = dt f(x) over component-major arrays.
+// Launch bounds for the stencil kernels of the backward pass: they are bound
+// by the latency of the neighbour gathers, so four resident blocks per SM
+// (at most 64 registers per thread) keep more loads in flight.
+constexpr int kAdjMinBlocks = 4;
+
 template <typename real, bool PREC, bool HSITE>
-__global__ void k_adj_rhs(const real* __restrict__ x, const real* __restrict__ hs, real* __restrict__ K, int nx, int ny,
+__global__ void __launch_bounds__(kAT, kAdjMinBlocks) k_adj_rhs(const real* __restrict__ x, const real* __restrict__ hs, real* __restrict__ K, int nx, int ny,
                           int nz, real J, real twoD, real H0, real H1, real H2, real lambda, real dt, int bc) {
     const long long N = (long long)nx * ny * nz;
     const real H[3] = {H0, H1, H2};
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
         long long nb[6];
-        neighbours(i, nx, ny, nz, nb);
         real wn[6];
-        neighbour_weights<real>(i, nx, ny, nz, bc, wn);
+        neighbours_w<real>(i, nx, ny, nz, bc, nb, wn);
         real h[3];
         heff_at<real, HSITE>(x, hs, i, nb, wn, N, J, twoD, H, h);
         real f[3];
@@ -134,40 +124,138 @@ __global__ void k_adj_rhs(const real* __restrict__ x, const real* __restrict__ h
     }
 }
 
-// out = s + sum_l coef[l] K_l over 3N elements.
+// out = s + sum_l coef[l] K_l: a stage input, or the RK combination y.  The
+// number of terms is a template argument (dispatched once on the host), so
+// the pointer table is indexed with constants and stays in kernel parameters.
 template <typename real>
 struct LinComb {
     const real* K[6];
     real coef[6];
-    int nk;
 };
 
-template <typename real>
+template <typename real, int NK>
+__device__ __forceinline__ real lincomb_at(const real* __restrict__ s, const LinComb<real>& lc, long long q) {
+    real acc = s[q];
+#pragma unroll
+    for (int l = 0; l < NK; ++l) acc += lc.coef[l] * lc.K[l][q];
+    return acc;
+}
+
+template <typename real, int NK>
 __global__ void k_adj_lincomb(real* __restrict__ out, const real* __restrict__ s, LinComb<real> lc, long long len) {
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < len; q += (long long)gridDim.x * blockDim.x) {
-        real acc = s[q];
-        for (int l = 0; l < lc.nk; ++l)
-            if (lc.coef[l] != real(0)) acc += lc.coef[l] * lc.K[l][q];
-        out[q] = acc;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < len; q += (long long)gridDim.x * blockDim.x)
+        out[q] = lincomb_at<real, NK>(s, lc, q);
+}
+
+// Stage transpose, site-local part ("w-part") at site i for the stage with
+// input x and v = dt lam_K: w and u, the per-site field gradient gseg += w,
+// and the site's terms of <w, sum_nn x> (J), 2 x_z w_z (D) and w (H) added to
+// the thread's partial sums p[5].
+template <typename real, bool PREC, bool HSITE>
+__device__ __forceinline__ void w_part(const real* __restrict__ x, const real* __restrict__ hs, long long i,
+                                       const long long nb[6], const real wn[6], long long N, real J, real twoD,
+                                       const real H[3], real lambda, const real v[3], real* __restrict__ w,
+                                       real* __restrict__ u, real* __restrict__ gseg, real p[5]) {
+    const real s[3] = {x[i], x[N + i], x[2 * N + i]};
+    real sn[3], hr[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const real* q = x + c * N;
+        sn[c] = wn[0] * q[nb[0]] + wn[1] * q[nb[1]] + wn[2] * q[nb[2]] + wn[3] * q[nb[3]] + wn[4] * q[nb[4]] +
+                wn[5] * q[nb[5]];
+        hr[c] = J * sn[c] + H[c];
+        if (HSITE) hr[c] += hs[c * N + i];
+    }
+    hr[2] += twoD * s[2];
+    // the transpose in the state precision (like the forward stages)
+    real a[3], sv[3], ssv[3], hv[3], av[3], hsv[3];
+    cross3r(s, hr, a);
+    cross3r(s, v, sv);
+    cross3r(s, sv, ssv);
+    cross3r(hr, v, hv);
+    cross3r(a, v, av);
+    cross3r(hr, sv, hsv);
+    real wi[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        real ui;
+        if (PREC) {
+            wi[c] = -sv[c] - lambda * ssv[c];
+            ui = hv[c] - lambda * av[c] + lambda * hsv[c];
+        } else {
+            wi[c] = -lambda * ssv[c];
+            ui = -lambda * av[c] + lambda * hsv[c];
+        }
+        w[c * N + i] = wi[c];
+        u[c * N + i] = ui;
+        if (gseg) gseg[c * N + i] += wi[c];
+    }
+    p[0] += wi[0] * sn[0] + wi[1] * sn[1] + wi[2] * sn[2];
+    p[1] += real(2) * s[2] * wi[2];
+    p[2] += wi[0];
+    p[3] += wi[1];
+    p[4] += wi[2];
+}
+
+// Block partials of the w-parts: the terms of one warp are summed in the
+// state precision (32 terms); the warp sums are converted once and added in
+// FP64 into the block's record, so the long sums over sites, stages and
+// steps are FP64 while the FP64 pipe (narrow on this GPU) sees a few
+// operations per warp instead of several per site.  Each block adds into its
+// own record, launch after launch in stream order (deterministic); the
+// records are summed once after the backward pass.
+template <typename real>
+__device__ __forceinline__ void flush_partials(real p[5], double* __restrict__ partials) {
+    __shared__ double red[kAT / 32][5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) p[q] += __shfl_xor_sync(0xffffffffu, p[q], o);
+    }
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+        for (int q = 0; q < 5; ++q) red[threadIdx.x >> 5][q] = (double)p[q];
+    __syncthreads();
+    if (threadIdx.x < 5) {
+        double t = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k][threadIdx.x];
+        partials[(long long)blockIdx.x * 5 + threadIdx.x] += t;
     }
 }
 
-// Pulse and renormalisation transposes, then lam_K_j = b_j lam_y and lam_s = lam_y.
+// Geometry and physics shared by the backward kernels.
+template <typename real>
+struct AdjGeom {
+    int nx, ny, nz, bc;
+    real J, twoD, H[3], lambda, dt;
+};
+
+// Top of the transposed step: pulse and renormalisation transposes, lam_s =
+// lam_y, lam_K_j = b_j lam_y (stored for j < S-1), then the w-part of the
+// last stage S-1, whose lam_K is not changed by any other stage.
 template <typename real>
 struct TopArgs {
     real* lam;           // in: dL/ds_after; out: lam_s = lam_y
-    const real* y;       // unnormalised RK result
+    const real* s;       // state before the step
+    LinComb<real> yc;    // y = s + sum_j b_j K_j, the unnormalised RK result
     real* LK[6];
     real b[6];
-    int S;
     int renorm, pulse;
     uint64_t seed, replica;
     long long k;
     real sigma;
+    const real* xlast;   // input of stage S-1
+    const real* hs;
+    real* w;             // w, u of stage S-1
+    real* u;
+    real* gseg;
+    double* partials;
 };
 
-template <typename real>
-__global__ void k_adj_top(TopArgs<real> a, long long N) {
+template <typename real, bool PREC, bool HSITE, int S>
+__global__ void __launch_bounds__(kAT, kAdjMinBlocks) k_adj_top_w(TopArgs<real> a, AdjGeom<real> G) {
+    const long long N = (long long)G.nx * G.ny * G.nz;
+    real p[5] = {0, 0, 0, 0, 0};
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
         real l0 = a.lam[i], l1 = a.lam[N + i], l2 = a.lam[2 * N + i];
         if (a.pulse) {
@@ -177,7 +265,8 @@ __global__ void k_adj_top(TopArgs<real> a, long long N) {
             pulse_rotate<real>(l0, l1, l2, -a.sigma * g0, -a.sigma * g1, -a.sigma * g2);
         }
         if (a.renorm) {
-            const real y0 = a.y[i], y1 = a.y[N + i], y2 = a.y[2 * N + i];
+            const real y0 = lincomb_at<real, S>(a.s, a.yc, i), y1 = lincomb_at<real, S>(a.s, a.yc, N + i),
+                       y2 = lincomb_at<real, S>(a.s, a.yc, 2 * N + i);
             const real n = Math<real>::sqrt_(y0 * y0 + y1 * y1 + y2 * y2);
             const real u0 = y0 / n, u1 = y1 / n, u2 = y2 / n;
             const real ul = u0 * l0 + u1 * l1 + u2 * l2;
@@ -188,113 +277,87 @@ __global__ void k_adj_top(TopArgs<real> a, long long N) {
         a.lam[i] = l0;
         a.lam[N + i] = l1;
         a.lam[2 * N + i] = l2;
-        for (int j = 0; j < a.S; ++j) {
+#pragma unroll
+        for (int j = 0; j < S - 1; ++j) {
             a.LK[j][i] = a.b[j] * l0;
             a.LK[j][N + i] = a.b[j] * l1;
             a.LK[j][2 * N + i] = a.b[j] * l2;
         }
-    }
-}
-
-// Stage transpose, site-local part: w and u at every site for v = dt lam_K,
-// plus FP64 block partials of <w, sum_nn x> (J), 2 x_z w_z (D) and w (H) and
-// the per-site field gradient gh += w.
-template <typename real, bool PREC, bool HSITE>
-__global__ void __launch_bounds__(kAT) k_adj_w(const real* __restrict__ x, const real* __restrict__ hs,
-                                               const real* __restrict__ LK, real* __restrict__ w, real* __restrict__ u,
-                                               double* __restrict__ gh, double* __restrict__ partials, int nx, int ny,
-                                               int nz, real J, real twoD, real H0, real H1, real H2, real lambda,
-                                               real dt, int bc) {
-    __shared__ double red[kAT / 32];
-    const long long N = (long long)nx * ny * nz;
-    const real H[3] = {H0, H1, H2};
-    double pJ = 0, pD = 0, pH0 = 0, pH1 = 0, pH2 = 0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
         long long nb[6];
-        neighbours(i, nx, ny, nz, nb);
         real wn[6];
-        neighbour_weights<real>(i, nx, ny, nz, bc, wn);
-        real hr[3];
-        heff_at<real, HSITE>(x, hs, i, nb, wn, N, J, twoD, H, hr);
-        // the transpose in the state precision (like the forward stages);
-        // the parameter gradients accumulate in FP64
-        const real s[3] = {x[i], x[N + i], x[2 * N + i]};
-        const real v[3] = {dt * LK[i], dt * LK[N + i], dt * LK[2 * N + i]};
-        real a[3], sv[3], ssv[3], hv[3], av[3], hsv[3];
-        cross3r(s, hr, a);
-        cross3r(s, v, sv);
-        cross3r(s, sv, ssv);
-        cross3r(hr, v, hv);
-        cross3r(a, v, av);
-        cross3r(hr, sv, hsv);
-        real wi[3], ui[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            if (PREC) {
-                wi[c] = -sv[c] - lambda * ssv[c];
-                ui[c] = hv[c] - lambda * av[c] + lambda * hsv[c];
-            } else {
-                wi[c] = -lambda * ssv[c];
-                ui[c] = -lambda * av[c] + lambda * hsv[c];
-            }
-            w[c * N + i] = wi[c];
-            u[c * N + i] = ui[c];
-            if (gh) gh[c * N + i] += (double)wi[c];
-        }
-        real sn[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const real* q = x + c * N;
-            sn[c] = wn[0] * q[nb[0]] + wn[1] * q[nb[1]] + wn[2] * q[nb[2]] + wn[3] * q[nb[3]] + wn[4] * q[nb[4]] +
-                    wn[5] * q[nb[5]];
-        }
-        pJ += (double)(wi[0] * sn[0] + wi[1] * sn[1] + wi[2] * sn[2]);
-        pD += (double)(real(2) * s[2] * wi[2]);
-        pH0 += (double)wi[0];
-        pH1 += (double)wi[1];
-        pH2 += (double)wi[2];
+        neighbours_w<real>(i, G.nx, G.ny, G.nz, G.bc, nb, wn);
+        const real bl = a.b[S - 1] * G.dt;
+        const real v[3] = {bl * l0, bl * l1, bl * l2};
+        w_part<real, PREC, HSITE>(a.xlast, a.hs, i, nb, wn, N, G.J, G.twoD, G.H, G.lambda, v, a.w, a.u, a.gseg, p);
     }
-    // each block adds into its own FP64 record, launch after launch in stream
-    // order (deterministic); the records are summed once after the backward pass
-    const double vals[5] = {pJ, pD, pH0, pH1, pH2};
-    for (int q = 0; q < 5; ++q) {
-        const double t = block_sum<double>(vals[q], red);
-        if (threadIdx.x == 0) partials[(long long)blockIdx.x * 5 + q] += t;
-    }
+    flush_partials<real>(p, a.partials);
 }
 
-// Stage transpose, neighbour part: lx = u + J sum_nn w + 2D w_z z, then
-// lam_s += lx and lam_K_l += a_jl lx for l < j.
+// Stage j of the transposed step: the neighbour part ("x-part") of stage j,
+// lx = u_j + J sum_nn w_j + 2D w_jz z, lam_s += lx, lam_K_l += a_jl lx (l < j),
+// and then (W) the w-part of stage j-1, which needs lam_K_{j-1} only at the
+// same site and is final once stage j's x-part has added to it.  w and u of
+// stage j are read from one buffer pair, those of stage j-1 written to the
+// other.
 template <typename real>
-struct XArgs {
-    const real* w;
+struct XWArgs {
+    const real* w;       // stage j
     const real* u;
     real* lam;
     real* LK[6];
-    real a[6];
-    int nl;
-    real J, twoD;
-    int bc;
+    real a[6];           // a_jl
+    const real* xprev;   // input of stage j-1
+    const real* hs;
+    real* wn;            // w, u of stage j-1
+    real* un;
+    real* gseg;
+    double* partials;
 };
 
-template <typename real>
-__global__ void k_adj_x(XArgs<real> a, int nx, int ny, int nz) {
-    const long long N = (long long)nx * ny * nz;
+template <typename real, bool PREC, bool HSITE, int NL, bool W>
+__global__ void __launch_bounds__(kAT, kAdjMinBlocks) k_adj_xw(XWArgs<real> a, AdjGeom<real> G) {
+    const long long N = (long long)G.nx * G.ny * G.nz;
+    real p[5] = {0, 0, 0, 0, 0};
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
         long long nb[6];
-        neighbours(i, nx, ny, nz, nb);
         real wn[6];
-        neighbour_weights<real>(i, nx, ny, nz, a.bc, wn);
+        neighbours_w<real>(i, G.nx, G.ny, G.nz, G.bc, nb, wn);
+        real lk[3] = {0, 0, 0};   // lam_K_{j-1} at the site after this stage
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const real* q = a.w + c * N;
-            real lx = a.u[c * N + i] + a.J * (wn[0] * q[nb[0]] + wn[1] * q[nb[1]] + wn[2] * q[nb[2]] + wn[3] * q[nb[3]] +
-                                              wn[4] * q[nb[4]] + wn[5] * q[nb[5]]);
-            if (c == 2) lx += a.twoD * a.w[2 * N + i];
+            real lx = a.u[c * N + i] + G.J * (wn[0] * q[nb[0]] + wn[1] * q[nb[1]] + wn[2] * q[nb[2]] +
+                                              wn[3] * q[nb[3]] + wn[4] * q[nb[4]] + wn[5] * q[nb[5]]);
+            if (c == 2) lx += G.twoD * a.w[2 * N + i];
             a.lam[c * N + i] += lx;
-            for (int l = 0; l < a.nl; ++l)
-                if (a.a[l] != real(0)) a.LK[l][c * N + i] += a.a[l] * lx;
+#pragma unroll
+            for (int l = 0; l < NL; ++l) {
+                if (a.a[l] != real(0)) {
+                    const real nv = a.LK[l][c * N + i] + a.a[l] * lx;
+                    a.LK[l][c * N + i] = nv;
+                    if (l == NL - 1) lk[c] = nv;
+                } else if (l == NL - 1) {
+                    lk[c] = a.LK[l][c * N + i];
+                }
+            }
         }
+        if (W) {
+            const real v[3] = {G.dt * lk[0], G.dt * lk[1], G.dt * lk[2]};
+            w_part<real, PREC, HSITE>(a.xprev, a.hs, i, nb, wn, N, G.J, G.twoD, G.H, G.lambda, v, a.wn, a.un,
+                                      a.gseg, p);
+        }
+    }
+    if (W) flush_partials<real>(p, a.partials);
+}
+
+// gh += gseg (FP64), gseg = 0: the field gradient of one checkpoint segment,
+// summed over its stages in the state precision, folded into the run's FP64
+// total.
+template <typename real>
+__global__ void k_adj_fold(double* __restrict__ gh, real* __restrict__ gseg, long long len) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < len; q += (long long)gridDim.x * blockDim.x) {
+        gh[q] += (double)gseg[q];
+        gseg[q] = real(0);
     }
 }
 
@@ -324,9 +387,8 @@ __global__ void __launch_bounds__(kAT) k_adj_seed(const real* __restrict__ s, co
     double bonds = 0, sz2 = 0, m0 = 0, m1 = 0, m2 = 0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
         long long nb[6];
-        neighbours(i, nx, ny, nz, nb);
         real wn[6];
-        neighbour_weights<real>(i, nx, ny, nz, bc, wn);
+        neighbours_w<real>(i, nx, ny, nz, bc, nb, wn);
         real h[3];
         heff_at<real, HSITE>(s, hs, i, nb, wn, N, J, twoD, H, h);
 #pragma unroll
@@ -392,11 +454,68 @@ size_t adjoint_workspace_bytes(const Geom& g, int elt, int stages, int K) {
     size_t b = 0;
     b += al(comp) * (size_t)(K + 1);     // segment states
     b += al(comp) * (size_t)stages * 3;  // X_j, K_j, lam_K_j
-    b += al(comp) * 5;                   // y, lam, w, u, scratch
+    b += al(comp) * 7;                   // y, lam, w and u (two pairs), segment field gradient
     b += al(sizeof(double) * 5 * (size_t)adjoint_blocks(g));
     b += al(sizeof(double) * 8);         // accumulators
     b += al(sizeof(long long));          // pulse-number slot
     return b;
+}
+
+// Launch the combine kernels with the term count as a template argument.
+template <typename real>
+void launch_lincomb(int nk, real* out, const real* s, const LinComb<real>& lc, long long len, cudaStream_t st) {
+    const int gb = grid_for(len);
+    switch (nk) {
+        case 0: k_adj_lincomb<real, 0><<<gb, kAT, 0, st>>>(out, s, lc, len); break;
+        case 1: k_adj_lincomb<real, 1><<<gb, kAT, 0, st>>>(out, s, lc, len); break;
+        case 2: k_adj_lincomb<real, 2><<<gb, kAT, 0, st>>>(out, s, lc, len); break;
+        case 3: k_adj_lincomb<real, 3><<<gb, kAT, 0, st>>>(out, s, lc, len); break;
+        case 4: k_adj_lincomb<real, 4><<<gb, kAT, 0, st>>>(out, s, lc, len); break;
+        default: k_adj_lincomb<real, 5><<<gb, kAT, 0, st>>>(out, s, lc, len); break;
+    }
+}
+
+template <typename real, bool PREC, bool HSITE>
+void launch_xw_t(int j, const XWArgs<real>& a, const AdjGeom<real>& G, int gb, cudaStream_t st) {
+    switch (j) {
+        case 0: k_adj_xw<real, PREC, HSITE, 0, false><<<gb, kAT, 0, st>>>(a, G); break;
+        case 1: k_adj_xw<real, PREC, HSITE, 1, true><<<gb, kAT, 0, st>>>(a, G); break;
+        case 2: k_adj_xw<real, PREC, HSITE, 2, true><<<gb, kAT, 0, st>>>(a, G); break;
+        case 3: k_adj_xw<real, PREC, HSITE, 3, true><<<gb, kAT, 0, st>>>(a, G); break;
+        case 4: k_adj_xw<real, PREC, HSITE, 4, true><<<gb, kAT, 0, st>>>(a, G); break;
+        default: k_adj_xw<real, PREC, HSITE, 5, true><<<gb, kAT, 0, st>>>(a, G); break;
+    }
+}
+
+// x-part of stage j and (j > 0) w-part of stage j-1.
+template <typename real>
+void launch_xw(bool prec, bool hsite, int j, const XWArgs<real>& a, const AdjGeom<real>& G, int gb, cudaStream_t st) {
+    if (prec) {
+        if (hsite) launch_xw_t<real, true, true>(j, a, G, gb, st);
+        else launch_xw_t<real, true, false>(j, a, G, gb, st);
+    } else {
+        if (hsite) launch_xw_t<real, false, true>(j, a, G, gb, st);
+        else launch_xw_t<real, false, false>(j, a, G, gb, st);
+    }
+}
+
+template <typename real, bool PREC, bool HSITE>
+void launch_top_w_t(int S, const TopArgs<real>& a, const AdjGeom<real>& G, int gb, cudaStream_t st) {
+    if (S == 2) k_adj_top_w<real, PREC, HSITE, 2><<<gb, kAT, 0, st>>>(a, G);
+    else if (S == 4) k_adj_top_w<real, PREC, HSITE, 4><<<gb, kAT, 0, st>>>(a, G);
+    else k_adj_top_w<real, PREC, HSITE, 6><<<gb, kAT, 0, st>>>(a, G);
+}
+
+template <typename real>
+void launch_top_w(bool prec, bool hsite, int S, const TopArgs<real>& a, const AdjGeom<real>& G, int gb,
+                  cudaStream_t st) {
+    if (prec) {
+        if (hsite) launch_top_w_t<real, true, true>(S, a, G, gb, st);
+        else launch_top_w_t<real, true, false>(S, a, G, gb, st);
+    } else {
+        if (hsite) launch_top_w_t<real, false, true>(S, a, G, gb, st);
+        else launch_top_w_t<real, false, false>(S, a, G, gb, st);
+    }
 }
 
 template <typename real>
@@ -430,11 +549,16 @@ cudaError_t adjoint_run(const AdjointRun<real>& A) {
     off += al(compb);
     real* lam = reinterpret_cast<real*>(ws + off);
     off += al(compb);
-    real* w = reinterpret_cast<real*>(ws + off);
+    real* wb[2];   // w and u of the stages, double-buffered by stage parity
+    real* ub[2];
+    for (int q = 0; q < 2; ++q) {
+        wb[q] = reinterpret_cast<real*>(ws + off);
+        off += al(compb);
+        ub[q] = reinterpret_cast<real*>(ws + off);
+        off += al(compb);
+    }
+    real* gseg = A.g_h ? reinterpret_cast<real*>(ws + off) : nullptr;  // field gradient of one segment
     off += al(compb);
-    real* u = reinterpret_cast<real*>(ws + off);
-    off += al(compb);
-    off += al(compb);  // scratch
     const int nb = adjoint_blocks(g);
     double* partials = reinterpret_cast<double*>(ws + off);
     off += al(sizeof(double) * 5 * (size_t)nb);
@@ -446,6 +570,18 @@ cudaError_t adjoint_run(const AdjointRun<real>& A) {
     const real lamb = (real)A.lambda, dt = (real)A.dt;
     const real* hs = A.h_site;
     const bool HS = hs != nullptr;
+    AdjGeom<real> G{};
+    G.nx = g.nx;
+    G.ny = g.ny;
+    G.nz = g.nz;
+    G.bc = A.bc;
+    G.J = J;
+    G.twoD = twoD;
+    G.H[0] = H0;
+    G.H[1] = H1;
+    G.H[2] = H2;
+    G.lambda = lamb;
+    G.dt = dt;
     cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(double) * 8, st);
     if (e != cudaSuccess) return e;
 
@@ -460,9 +596,11 @@ cudaError_t adjoint_run(const AdjointRun<real>& A) {
                                                     H2, A.dLdE, A.dLdM[0], A.dLdM[1], A.dLdM[2], A.bc);
     k_adj_seed_finish<<<1, kAT, 0, st>>>(partials, nb, acc, A.dLdE, (double)N);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    // per-block FP64 records of the stage transposes start at zero
+    // per-block FP64 records of the stage transposes and the segment field
+    // gradient start at zero
     e = cudaMemsetAsync(partials, 0, sizeof(double) * 5 * (size_t)nb, st);
     if (e != cudaSuccess) return e;
+    if (gseg && (e = cudaMemsetAsync(gseg, 0, compb, st)) != cudaSuccess) return e;
 
     const long long total = A.n_end - A.n0;
     const int nseg = (int)((total + A.K - 1) / A.K);
@@ -497,71 +635,74 @@ cudaError_t adjoint_run(const AdjointRun<real>& A) {
             const long long n = start + m;
             const bool pul = A.noise && (n % A.R) == (A.R / 2);
             const real* s = seg + (size_t)(m - 1) * len;
-            // stages X_j and K_j = dt f(X_j), and y = s + sum b_j K_j
+            // stages X_j and K_j = dt f(X_j); the first stage's input is s itself
+            const real* Xs[6];
             for (int j = 0; j < S; ++j) {
-                LinComb<real> lc{};
-                for (int l = 0; l < j; ++l) {
-                    lc.K[l] = Kst[l];
-                    lc.coef[l] = (real)tb.a[j][l];
-                }
-                lc.nk = j;
-                k_adj_lincomb<real><<<grid_for(len), kAT, 0, st>>>(X[j], s, lc, len);
-                if (A.precession) {
-                    if (HS) k_adj_rhs<real, true, true><<<grid_for(N), kAT, 0, st>>>(X[j], hs, Kst[j], g.nx, g.ny, g.nz, J, twoD, H0, H1, H2, lamb, dt, A.bc);
-                    else k_adj_rhs<real, true, false><<<grid_for(N), kAT, 0, st>>>(X[j], nullptr, Kst[j], g.nx, g.ny, g.nz, J, twoD, H0, H1, H2, lamb, dt, A.bc);
+                if (j == 0) {
+                    Xs[0] = s;
                 } else {
-                    if (HS) k_adj_rhs<real, false, true><<<grid_for(N), kAT, 0, st>>>(X[j], hs, Kst[j], g.nx, g.ny, g.nz, J, twoD, H0, H1, H2, lamb, dt, A.bc);
-                    else k_adj_rhs<real, false, false><<<grid_for(N), kAT, 0, st>>>(X[j], nullptr, Kst[j], g.nx, g.ny, g.nz, J, twoD, H0, H1, H2, lamb, dt, A.bc);
+                    LinComb<real> lc{};
+                    for (int l = 0; l < j; ++l) {
+                        lc.K[l] = Kst[l];
+                        lc.coef[l] = (real)tb.a[j][l];
+                    }
+                    launch_lincomb<real>(j, X[j], s, lc, len, st);
+                    Xs[j] = X[j];
                 }
-            }
-            {
-                LinComb<real> lc{};
-                for (int l = 0; l < S; ++l) {
-                    lc.K[l] = Kst[l];
-                    lc.coef[l] = (real)tb.b[l];
+                if (A.precession) {
+                    if (HS) k_adj_rhs<real, true, true><<<grid_for(N), kAT, 0, st>>>(Xs[j], hs, Kst[j], g.nx, g.ny, g.nz, J, twoD, H0, H1, H2, lamb, dt, A.bc);
+                    else k_adj_rhs<real, true, false><<<grid_for(N), kAT, 0, st>>>(Xs[j], nullptr, Kst[j], g.nx, g.ny, g.nz, J, twoD, H0, H1, H2, lamb, dt, A.bc);
+                } else {
+                    if (HS) k_adj_rhs<real, false, true><<<grid_for(N), kAT, 0, st>>>(Xs[j], hs, Kst[j], g.nx, g.ny, g.nz, J, twoD, H0, H1, H2, lamb, dt, A.bc);
+                    else k_adj_rhs<real, false, false><<<grid_for(N), kAT, 0, st>>>(Xs[j], nullptr, Kst[j], g.nx, g.ny, g.nz, J, twoD, H0, H1, H2, lamb, dt, A.bc);
                 }
-                lc.nk = S;
-                k_adj_lincomb<real><<<grid_for(len), kAT, 0, st>>>(y, s, lc, len);
             }
             TopArgs<real> ta{};
             ta.lam = lam;
-            ta.y = y;
+            ta.s = s;
+            for (int l = 0; l < S; ++l) {
+                ta.yc.K[l] = Kst[l];
+                ta.yc.coef[l] = (real)tb.b[l];
+            }
             for (int j = 0; j < S; ++j) {
                 ta.LK[j] = LK[j];
                 ta.b[j] = (real)tb.b[j];
             }
-            ta.S = S;
             ta.renorm = A.renorm;
             ta.pulse = pul ? 1 : 0;
             ta.seed = A.seed;
             ta.replica = A.replica;
             ta.k = (n - 1) / A.R;
             ta.sigma = (real)A.sigma;
-            k_adj_top<real><<<grid_for(N), kAT, 0, st>>>(ta, N);
+            ta.xlast = Xs[S - 1];
+            ta.hs = hs;
+            ta.w = wb[(S - 1) & 1];
+            ta.u = ub[(S - 1) & 1];
+            ta.gseg = gseg;
+            ta.partials = partials;
+            launch_top_w<real>(A.precession != 0, HS, S, ta, G, nb, st);
             for (int j = S - 1; j >= 0; --j) {
-                if (A.precession) {
-                    if (HS) k_adj_w<real, true, true><<<nb, kAT, 0, st>>>(X[j], hs, LK[j], w, u, A.g_h, partials, g.nx, g.ny, g.nz, J, twoD, H0, H1, H2, lamb, dt, A.bc);
-                    else k_adj_w<real, true, false><<<nb, kAT, 0, st>>>(X[j], nullptr, LK[j], w, u, A.g_h, partials, g.nx, g.ny, g.nz, J, twoD, H0, H1, H2, lamb, dt, A.bc);
-                } else {
-                    if (HS) k_adj_w<real, false, true><<<nb, kAT, 0, st>>>(X[j], hs, LK[j], w, u, A.g_h, partials, g.nx, g.ny, g.nz, J, twoD, H0, H1, H2, lamb, dt, A.bc);
-                    else k_adj_w<real, false, false><<<nb, kAT, 0, st>>>(X[j], nullptr, LK[j], w, u, A.g_h, partials, g.nx, g.ny, g.nz, J, twoD, H0, H1, H2, lamb, dt, A.bc);
-                }
-                XArgs<real> xa{};
-                xa.w = w;
-                xa.u = u;
+                XWArgs<real> xa{};
+                xa.w = wb[j & 1];
+                xa.u = ub[j & 1];
                 xa.lam = lam;
                 for (int l = 0; l < j; ++l) {
                     xa.LK[l] = LK[l];
                     xa.a[l] = (real)tb.a[j][l];
                 }
-                xa.nl = j;
-                xa.J = J;
-                xa.twoD = twoD;
-                xa.bc = A.bc;
-                k_adj_x<real><<<grid_for(N), kAT, 0, st>>>(xa, g.nx, g.ny, g.nz);
+                if (j > 0) {
+                    xa.xprev = Xs[j - 1];
+                    xa.wn = wb[(j - 1) & 1];
+                    xa.un = ub[(j - 1) & 1];
+                }
+                xa.hs = hs;
+                xa.gseg = gseg;
+                xa.partials = partials;
+                launch_xw<real>(A.precession != 0, HS, j, xa, G, nb, st);
             }
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
+        if (gseg) k_adj_fold<real><<<grid_for(len), kAT, 0, st>>>(A.g_h, gseg, len);
     }
     k_adj_accumulate<<<1, kAT, 0, st>>>(partials, nb, acc, 1.0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
