@@ -18,15 +18,11 @@ struct Words4 {
     uint64_t w[4];
 };
 
-// 64x64 -> 128-bit product from four 32x32 -> 64 partial products.
+// 64x64 -> 128-bit product: low word by the wrapping multiply, high word by
+// the compiler's multiply-high intrinsic.
 __device__ __forceinline__ void mul64_wide(uint64_t a, uint64_t m, uint64_t& hi, uint64_t& lo) {
-    const uint32_t a0 = (uint32_t)a, a1 = (uint32_t)(a >> 32);
-    const uint32_t m0 = (uint32_t)m, m1 = (uint32_t)(m >> 32);
-    const uint64_t p00 = (uint64_t)a0 * m0, p01 = (uint64_t)a0 * m1;
-    const uint64_t p10 = (uint64_t)a1 * m0, p11 = (uint64_t)a1 * m1;
-    const uint64_t mid = (p00 >> 32) + (uint32_t)p01 + (uint32_t)p10;
-    lo = (mid << 32) | (uint32_t)p00;
-    hi = p11 + (p01 >> 32) + (p10 >> 32) + (mid >> 32);
+    lo = a * m;
+    hi = __umul64hi(a, m);
 }
 
 __device__ __forceinline__ Words4 philox4x64_10(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3,
