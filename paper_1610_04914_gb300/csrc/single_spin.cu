@@ -47,18 +47,44 @@ struct SingleCommon {
     uint64_t seed;
 };
 
-// One step of the integrator with ST stages on one spin, then |s| = 1.  RECT:
+// Which stage couplings a_jl and weights b_j of each integrator are nonzero
+// (RK4, Butcher RK5, RK2 midpoint, Heun: the structure of the tableaus of
+// tableau_for, whose values the kernels read); zero terms are skipped at
+// compile time.  tableau_mask_matches checks the two agree before a launch.
+__host__ __device__ constexpr int integ_stages(int integ) { return integ == 0 ? 4 : integ == 1 ? 6 : 2; }
+__host__ __device__ constexpr bool a_nonzero(int integ, int j, int l) {
+    return integ == 0 ? l == j - 1
+         : integ == 1 ? !((j == 3 && l == 0) || (j == 4 && (l == 1 || l == 2)))
+                      : (j == 1 && l == 0);
+}
+__host__ __device__ constexpr bool b_nonzero(int integ, int j) {
+    return integ == 1 ? j != 1 : integ == 2 ? j == 1 : true;
+}
+
+bool tableau_mask_matches(int integ, const Tableau& tb) {
+    if (tb.stages != integ_stages(integ)) return false;
+    for (int j = 0; j < tb.stages; ++j) {
+        if (!b_nonzero(integ, j) && tb.b[j] != 0.0) return false;
+        for (int l = 0; l < j; ++l)
+            if (!a_nonzero(integ, j, l) && tb.a[j][l] != 0.0) return false;
+    }
+    return true;
+}
+
+// One step of integrator INTEG on one spin, then |s| = 1.  RECT:
 // the rectangular-noise field z is added to H_eff in the precession term of
 // every stage (Eqs. (LLL), (zeta_n)); otherwise the noiseless equation.
-template <typename real, bool PREC, int ST, bool RECT>
+template <typename real, bool PREC, int INTEG, bool RECT>
 __device__ __forceinline__ void single_step(real& s0, real& s1, real& s2, real lam, const SingleCommon<real>& C,
                                             real z0, real z1, real z2) {
+    constexpr int ST = integ_stages(INTEG);
     real K[ST][3];
 #pragma unroll
     for (int j = 0; j < ST; ++j) {
         real x0 = s0, x1 = s1, x2 = s2;
 #pragma unroll
         for (int l = 0; l < j; ++l) {
+            if (!a_nonzero(INTEG, j, l)) continue;
             const real c = C.a[j][l];
             x0 += c * K[l][0];
             x1 += c * K[l][1];
@@ -75,6 +101,7 @@ __device__ __forceinline__ void single_step(real& s0, real& s1, real& s2, real l
     }
 #pragma unroll
     for (int j = 0; j < ST; ++j) {
+        if (!b_nonzero(INTEG, j)) continue;
         s0 += C.b[j] * K[j][0];
         s1 += C.b[j] * K[j][1];
         s2 += C.b[j] * K[j][2];
@@ -107,7 +134,7 @@ struct RunArgs {
     int stop;
 };
 
-template <typename real, bool PREC, int ST, bool RECT>
+template <typename real, bool PREC, int INTEG, bool RECT>
 __global__ void __launch_bounds__(128) k_single_run(RunArgs<real> A) {
     const SingleCommon<real>& C = A.c;
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -127,7 +154,7 @@ __global__ void __launch_bounds__(128) k_single_run(RunArgs<real> A) {
     if (RECT && ph != 0) draw_zeta<real>(C, (uint64_t)kq, (uint64_t)r, sig, z0, z1, z2);  // mid-interval start
     for (long long n = A.n0 + 1; n <= A.n0 + A.nsteps; ++n) {
         if (RECT && ph == 0) draw_zeta<real>(C, (uint64_t)kq, (uint64_t)r, sig, z0, z1, z2);  // interval (n-1) div R
-        single_step<real, PREC, ST, RECT>(s0, s1, s2, lam, C, z0, z1, z2);
+        single_step<real, PREC, INTEG, RECT>(s0, s1, s2, lam, C, z0, z1, z2);
         if (++ph == C.R) {
             ph = 0;
             ++kq;
@@ -172,7 +199,7 @@ struct EscapeArgs {
 // n with n mod R == 0 and starts its next trial there, so that every trial
 // sees the schedule of a fresh run: pulse after local step R/2 of each
 // interval, pulse number counted from the trial's start.
-template <typename real, bool PREC, int ST, bool RECT>
+template <typename real, bool PREC, int INTEG, bool RECT>
 __global__ void __launch_bounds__(128) k_single_escape(EscapeArgs<real> A) {
     const SingleCommon<real>& C = A.c;
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -195,7 +222,7 @@ __global__ void __launch_bounds__(128) k_single_escape(EscapeArgs<real> A) {
     if (RECT && ph != 0) draw_zeta<real>(C, (uint64_t)mk, rep0 + (uint64_t)j * nrep, sig, z0, z1, z2);
     for (long long it = 0; it < A.nsteps; ++it) {
         if (RECT && ph == 0) draw_zeta<real>(C, (uint64_t)mk, rep0 + (uint64_t)j * nrep, sig, z0, z1, z2);
-        single_step<real, PREC, ST, RECT>(s0, s1, s2, lam, C, z0, z1, z2);
+        single_step<real, PREC, INTEG, RECT>(s0, s1, s2, lam, C, z0, z1, z2);
         if (++ph == C.R) ph = 0;
         m += running;
         mk += running && ph == 0;
@@ -256,25 +283,26 @@ SingleCommon<real> make_common(const spin_params* p, int nrep, void* s, void* sc
     return C;
 }
 
-template <typename real, bool PREC, int ST, bool RECT>
+template <typename real, bool PREC, int INTEG, bool RECT>
 struct RunK {
     static void launch(int blocks, cudaStream_t st, const RunArgs<real>& A) {
-        k_single_run<real, PREC, ST, RECT><<<blocks, 128, 0, st>>>(A);
+        k_single_run<real, PREC, INTEG, RECT><<<blocks, 128, 0, st>>>(A);
     }
 };
-template <typename real, bool PREC, int ST, bool RECT>
+template <typename real, bool PREC, int INTEG, bool RECT>
 struct EscK {
     static void launch(int blocks, cudaStream_t st, const EscapeArgs<real>& A) {
-        k_single_escape<real, PREC, ST, RECT><<<blocks, 128, 0, st>>>(A);
+        k_single_escape<real, PREC, INTEG, RECT><<<blocks, 128, 0, st>>>(A);
     }
 };
 
-// Launch Kern<real, PREC, stages, RECT> for the integrator, the precession
+// Launch Kern<real, PREC, integrator, RECT> for the integrator, the precession
 // flag and the noise kind (rectangular noise needs the precession term).
 template <typename real, template <typename, bool, int, bool> class Kern, typename Args>
 cudaError_t dispatch(const spin_params* p, int nrep, const Args& A, cudaStream_t st) {
     const int blocks = (nrep + 127) / 128;
-    const int ns = tableau_for(p->integrator).stages;
+    if (!tableau_mask_matches(p->integrator, tableau_for(p->integrator))) return cudaErrorInvalidValue;
+    const int ns = p->integrator;
     const bool prec = p->precession != 0;
     const bool rect = p->noise == 2;
 #define SPIN_SINGLE_CASE(NS)                                     \
@@ -287,9 +315,10 @@ cudaError_t dispatch(const spin_params* p, int nrep, const Args& A, cudaStream_t
             Kern<real, false, NS, false>::launch(blocks, st, A); \
         break;
     switch (ns) {
+        SPIN_SINGLE_CASE(0)
+        SPIN_SINGLE_CASE(1)
         SPIN_SINGLE_CASE(2)
-        SPIN_SINGLE_CASE(4)
-        SPIN_SINGLE_CASE(6)
+        SPIN_SINGLE_CASE(3)
         default:
             return cudaErrorInvalidValue;
     }
