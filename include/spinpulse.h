@@ -47,7 +47,7 @@ typedef enum spin_status {
     SPIN_ECUDA = -2,             /* a CUDA runtime call failed; detail in spin_last_error */
     SPIN_ENONFINITE = -3,        /* a spin became NaN/Inf (integration unstable) */
     SPIN_ETIMEOUT = -4,          /* a bounded device wait gave up */
-    SPIN_EUNSUPPORTED = -5,      /* valid request this build does not implement */
+    SPIN_EUNSUPPORTED = -5,      /* valid request the library does not implement */
     SPIN_ENOSPACE = -6           /* workspace smaller than spin_workspace_size() */
 } spin_status;
 
