@@ -67,7 +67,16 @@ struct PatchArgs {
     float sigma;
     const long long* interval;
     int bc;            // 1: free boundaries (outside columns and planes read as zero spins)
+    int pair8;         // 1: each thread's column pair is one aligned 8-byte word of every input plane
 };
+
+// A column pair (2m, 2m+1) is contiguous in a row of even length and never
+// straddles the periodic wrap; with 8-byte aligned component arrays it can be
+// fetched as one 8-byte copy.
+__host__ __device__ __forceinline__ bool pairs_aligned(int nx, const float* p0, const float* p1, const float* p2) {
+    return (nx & 1) == 0 && ((reinterpret_cast<unsigned long long>(p0) | reinterpret_cast<unsigned long long>(p1) |
+                              reinterpret_cast<unsigned long long>(p2)) & 7ULL) == 0;
+}
 
 typedef float2 f2;
 #ifndef SPIN_NO_F32X2
@@ -85,6 +94,10 @@ __device__ __forceinline__ f2 sp2(float v) { return make_float2(v, v); }
 __device__ __forceinline__ void cp_async4(float* smem, const float* gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(float* smem, const float* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
@@ -119,11 +132,12 @@ struct PThread {
 
 // Per-thread staging ring for spin planes fetched two iterations ahead with
 // cp.async (the thread only ever reads back its own columns): 4 slots x 3
-// components x PY rows x 2 columns, thread-minor so accesses are conflict-free.
+// components x PY rows, one column pair (two adjacent floats) per thread,
+// thread-minor, so the pair is one conflict-free 8-byte access.
 template <int S>
-__device__ __forceinline__ float* stage_slot(float* stg, int slot, int c, int rr, int e, int tid) {
+__device__ __forceinline__ float* stage_pair(float* stg, int slot, int c, int rr, int tid) {
     constexpr int PY = PatchShape<S>::PY, NT = kPT * PatchShape<S>::TY;
-    return stg + (((slot * 3 + c) * PY + rr) * 2 + e) * NT + tid;
+    return stg + 2 * ((((slot * 3 + c) * PY + rr) * NT) + tid);
 }
 
 template <int S>
@@ -131,15 +145,25 @@ __device__ __forceinline__ void issue_plane(const PatchArgs& a, float* stg, cons
                                             int slot, int gz, int tid) {
     constexpr int PY = PatchShape<S>::PY;
     const long long base = (long long)gz * th.plane;
+    if (a.pair8) {
 #pragma unroll
-    for (int rr = 0; rr < PY; ++rr)
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            const long long o = base + th.col[rr][e];
-            cp_async4(stage_slot<S>(stg, slot, 0, rr, e, tid), a.in0 + o);
-            cp_async4(stage_slot<S>(stg, slot, 1, rr, e, tid), a.in1 + o);
-            cp_async4(stage_slot<S>(stg, slot, 2, rr, e, tid), a.in2 + o);
+        for (int rr = 0; rr < PY; ++rr) {
+            const long long o = base + th.col[rr][0];
+            cp_async8(stage_pair<S>(stg, slot, 0, rr, tid), a.in0 + o);
+            cp_async8(stage_pair<S>(stg, slot, 1, rr, tid), a.in1 + o);
+            cp_async8(stage_pair<S>(stg, slot, 2, rr, tid), a.in2 + o);
         }
+    } else {
+#pragma unroll
+        for (int rr = 0; rr < PY; ++rr)
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const long long o = base + th.col[rr][e];
+                cp_async4(stage_pair<S>(stg, slot, 0, rr, tid) + e, a.in0 + o);
+                cp_async4(stage_pair<S>(stg, slot, 1, rr, tid) + e, a.in1 + o);
+                cp_async4(stage_pair<S>(stg, slot, 2, rr, tid) + e, a.in2 + o);
+            }
+    }
     cp_async_commit();
 }
 
@@ -178,8 +202,7 @@ __device__ __forceinline__ void patch_iteration(const PatchArgs& a, PRings<S, HS
         for (int rr = 0; rr < PY; ++rr)
 #pragma unroll
             for (int c = 0; c < 3; ++c)
-                r.s[slot][rr][c] = make_float2(*stage_slot<S>(stg, slot, c, rr, 0, tid),
-                                               *stage_slot<S>(stg, slot, c, rr, 1, tid));
+                r.s[slot][rr][c] = *reinterpret_cast<const f2*>(stage_pair<S>(stg, slot, c, rr, tid));
         if (a.bc) {
             // free boundaries: no spin outside the lattice (a zero spin stays
             // zero through every stage, so it never feeds the stencil)
@@ -232,15 +255,15 @@ __device__ __forceinline__ void patch_iteration(const PatchArgs& a, PRings<S, HS
                     // x-neighbours: left of the pair's first column and right of its second
                     const float L = __shfl_up_sync(0xffffffffu, C.y, 1, kPT);
                     const float Rr = __shfl_down_sync(0xffffffffu, C.x, 1, kPT);
-                    const f2 xm = make_float2(L, C.x);
-                    const f2 xp = make_float2(C.y, Rr);
+                    // (x-1) + (x+1) for both columns of the pair, as two scalar adds
+                    const f2 xs = make_float2(__fadd_rn(L, C.y), __fadd_rn(C.x, Rr));
                     const int ro = PY == 2 ? (rr ^ 1) : rr;
                     const f2 other = (j == 1) ? r.s[slot][ro][c] : r.x[j - 2][slot][ro][c];
                     const f2 ym = rr == 0 ? row_up : other;
                     const f2 yp = rr == PY - 1 ? row_dn : other;
                     // ((x-1 + x+1) + (y-1 + y+1)) + z-1, and z+1 last: it is the
                     // value the previous stage produced in this iteration
-                    sum[rr][c] = add2(add2(add2(add2(xm, xp), add2(ym, yp)), ZM), ZP);
+                    sum[rr][c] = add2(add2(add2(xs, add2(ym, yp)), ZM), ZP);
                     cen[rr][c] = C;
                 }
             }
@@ -417,6 +440,7 @@ __global__ void __launch_bounds__(kPT* PatchShape<S>::TY, 1)
     a.out1 += rp.off;
     a.out2 += rp.off;
     a.nx = a.ny = a.nz = rp.L;
+    a.pair8 = pairs_aligned(rp.L, a.in0, a.in1, a.in2) ? 1 : 0;
     a.tz = rp.tz;
     a.n_iter = rp.tz + 2 * S - 2;
     a.sigma = rp.sigma;
@@ -518,6 +542,7 @@ PatchArgs patch_args_common(const StepLaunch<float>& L) {
     a.renorm = L.renorm;
     a.seed = L.seed;
     a.replica = L.replica;
+    a.pair8 = pairs_aligned(a.nx, a.in0, a.in1, a.in2) ? 1 : 0;
     a.sigma = L.sigma;
     a.interval = L.d_interval;
     a.bc = L.bc;
