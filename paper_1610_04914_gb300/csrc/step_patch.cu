@@ -68,6 +68,7 @@ struct PatchArgs {
     const long long* interval;
     int bc;            // 1: free boundaries (outside columns and planes read as zero spins)
     int pair8;         // 1: each thread's column pair is one aligned 8-byte word of every input plane
+    int pair8out;      // 1: the same for the output planes
 };
 
 // A column pair (2m, 2m+1) is contiguous in a row of even length and never
@@ -320,6 +321,17 @@ __device__ __forceinline__ void patch_iteration(const PatchArgs& a, PRings<S, HS
                     oy = mul2(oy, inv);
                     oz = mul2(oz, inv);
                 }
+                if (!PULSE && a.pair8out) {
+                    // both columns of the pair are outputs or neither (even row
+                    // length, even tile offsets): one 8-byte store per component
+                    if (th.out[rr][0]) {
+                        const long long site = base + th.col[rr][0];
+                        *reinterpret_cast<f2*>(a.out0 + site) = ox;
+                        *reinterpret_cast<f2*>(a.out1 + site) = oy;
+                        *reinterpret_cast<f2*>(a.out2 + site) = oz;
+                    }
+                    continue;
+                }
                 float vx[2] = {ox.x, ox.y}, vy[2] = {oy.x, oy.y}, vz[2] = {oz.x, oz.y};
 #pragma unroll
                 for (int e = 0; e < 2; ++e) {
@@ -441,6 +453,7 @@ __global__ void __launch_bounds__(kPT* PatchShape<S>::TY, 1)
     a.out2 += rp.off;
     a.nx = a.ny = a.nz = rp.L;
     a.pair8 = pairs_aligned(rp.L, a.in0, a.in1, a.in2) ? 1 : 0;
+    a.pair8out = pairs_aligned(rp.L, a.out0, a.out1, a.out2) ? 1 : 0;
     a.tz = rp.tz;
     a.n_iter = rp.tz + 2 * S - 2;
     a.sigma = rp.sigma;
@@ -543,6 +556,7 @@ PatchArgs patch_args_common(const StepLaunch<float>& L) {
     a.seed = L.seed;
     a.replica = L.replica;
     a.pair8 = pairs_aligned(a.nx, a.in0, a.in1, a.in2) ? 1 : 0;
+    a.pair8out = pairs_aligned(a.nx, a.out0, a.out1, a.out2) ? 1 : 0;
     a.sigma = L.sigma;
     a.interval = L.d_interval;
     a.bc = L.bc;
