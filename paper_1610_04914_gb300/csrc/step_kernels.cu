@@ -390,23 +390,30 @@ struct Vec3P {
     const real* p[3];
 };
 
-// K = dt f(x) over the lattice; neighbours read from global memory.
+// K = dt f(x) over the lattice; neighbours read from global memory.  Blocks
+// of kGX threads along x on a (x tile, row) grid: one integer division per row
+// (y, z), none per site; periodic neighbours wrap by comparison.
+constexpr int kGX = 128;
+
 template <typename real, bool PREC, bool HSITE>
-__global__ void k_stage_rhs(Vec3P<real> x, Vec3P<real> hs, real* __restrict__ K0, real* __restrict__ K1,
-                            real* __restrict__ K2, int nx, int ny, int nz, Phys<real> ph, real dt, int bc) {
-    const long long N = (long long)nx * ny * nz;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int xi = (int)(i % nx);
-        const int yi = (int)((i / nx) % ny);
-        const int zi = (int)(i / ((long long)nx * ny));
-        const long long P = (long long)nx * ny;
-        const long long rowb = i - xi;
-        const long long nb[6] = {rowb + wrap_index(xi - 1, nx), rowb + wrap_index(xi + 1, nx),
-                                 (long long)zi * P + (long long)wrap_index(yi - 1, ny) * nx + xi,
-                                 (long long)zi * P + (long long)wrap_index(yi + 1, ny) * nx + xi,
-                                 (long long)wrap_index(zi - 1, nz) * P + (long long)yi * nx + xi,
-                                 (long long)wrap_index(zi + 1, nz) * P + (long long)yi * nx + xi};
+__global__ void __launch_bounds__(kGX) k_stage_rhs(Vec3P<real> x, Vec3P<real> hs, real* __restrict__ K0,
+                                                   real* __restrict__ K1, real* __restrict__ K2, int nx, int ny,
+                                                   int nz, Phys<real> ph, real dt, int bc) {
+    const int xi = blockIdx.x * kGX + threadIdx.x;
+    if (xi >= nx) return;
+    const long long P = (long long)nx * ny;
+    const long long N = P * nz;
+    const int rows = ny * nz;
+    for (int row = blockIdx.y; row < rows; row += gridDim.y) {
+        const int zi = row / ny;
+        const int yi = row - zi * ny;
+        const long long i = (long long)row * nx + xi;
+        const long long nb[6] = {xi > 0 ? i - 1 : i + (nx - 1),
+                                 xi < nx - 1 ? i + 1 : i - (nx - 1),
+                                 yi > 0 ? i - nx : i + (long long)(ny - 1) * nx,
+                                 yi < ny - 1 ? i + nx : i - (long long)(ny - 1) * nx,
+                                 zi > 0 ? i - P : i + (N - P),
+                                 zi < nz - 1 ? i + P : i - (N - P)};
         // free boundaries: a neighbour across a face does not exist
         const real w[6] = {(bc && xi == 0) ? real(0) : real(1), (bc && xi == nx - 1) ? real(0) : real(1),
                            (bc && yi == 0) ? real(0) : real(1), (bc && yi == ny - 1) ? real(0) : real(1),
@@ -443,8 +450,10 @@ struct CombineArgs {
     const long long* interval;
 };
 
-// out = s + sum_l coef[l] K_l, optionally renormalised and pulsed.
-template <typename real>
+// out = s + sum_l coef[l] K_l, optionally renormalised and pulsed.  The term
+// count NK is a template argument (dispatched on the host), so the pointer
+// table is indexed with constants and stays in the kernel parameters.
+template <typename real, int NK>
 __global__ void k_combine(CombineArgs<real> a, long long N) {
     const long long k = a.pulse ? *a.interval : 0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
@@ -453,7 +462,8 @@ __global__ void k_combine(CombineArgs<real> a, long long N) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             real acc = a.s[c][i];
-            for (int l = 0; l < a.nk; ++l)
+#pragma unroll
+            for (int l = 0; l < NK; ++l)
                 if (a.coef[l] != real(0)) acc += a.coef[l] * a.K[l][c * N + i];
             v[c] = acc;
         }
@@ -471,6 +481,18 @@ __global__ void k_combine(CombineArgs<real> a, long long N) {
 }
 
 template <typename real>
+static void launch_combine(int nk, const CombineArgs<real>& c, long long N, int blocks, int threads, cudaStream_t st) {
+    switch (nk) {
+        case 1: k_combine<real, 1><<<blocks, threads, 0, st>>>(c, N); break;
+        case 2: k_combine<real, 2><<<blocks, threads, 0, st>>>(c, N); break;
+        case 3: k_combine<real, 3><<<blocks, threads, 0, st>>>(c, N); break;
+        case 4: k_combine<real, 4><<<blocks, threads, 0, st>>>(c, N); break;
+        case 5: k_combine<real, 5><<<blocks, threads, 0, st>>>(c, N); break;
+        default: k_combine<real, 6><<<blocks, threads, 0, st>>>(c, N); break;
+    }
+}
+
+template <typename real>
 static cudaError_t launch_generic(const StepLaunch<real>& L) {
     const Tableau& tb = *L.tab;
     const long long N = L.g.N();
@@ -482,6 +504,8 @@ static cudaError_t launch_generic(const StepLaunch<real>& L) {
     real* xs = L.tmp + (size_t)tb.stages * 3 * N;
     const bool hs = L.hs[0] != nullptr;
     Vec3P<real> hv{{L.hs[0], L.hs[1], L.hs[2]}};
+    const long long rows = (long long)L.g.ny * L.g.nz;
+    const dim3 rgrid((L.g.nx + kGX - 1) / kGX, (unsigned)std::min<long long>(rows, 65535));
     for (int j = 0; j < tb.stages; ++j) {
         Vec3P<real> xv;
         if (j == 0) {
@@ -497,20 +521,20 @@ static cudaError_t launch_generic(const StepLaunch<real>& L) {
                 c.coef[l] = (real)tb.a[j][l];
             }
             c.nk = j;
-            k_combine<real><<<blocks, threads, 0, L.stream>>>(c, N);
+            launch_combine<real>(j, c, N, blocks, threads, L.stream);
             xv = Vec3P<real>{{xs, xs + N, xs + 2 * N}};
         }
         real* k0 = K[j];
         if (L.precession) {
             if (hs)
-                k_stage_rhs<real, true, true><<<blocks, threads, 0, L.stream>>>(xv, hv, k0, k0 + N, k0 + 2 * N, L.g.nx, L.g.ny, L.g.nz, L.ph, (real)L.dt, L.bc);
+                k_stage_rhs<real, true, true><<<rgrid, kGX, 0, L.stream>>>(xv, hv, k0, k0 + N, k0 + 2 * N, L.g.nx, L.g.ny, L.g.nz, L.ph, (real)L.dt, L.bc);
             else
-                k_stage_rhs<real, true, false><<<blocks, threads, 0, L.stream>>>(xv, hv, k0, k0 + N, k0 + 2 * N, L.g.nx, L.g.ny, L.g.nz, L.ph, (real)L.dt, L.bc);
+                k_stage_rhs<real, true, false><<<rgrid, kGX, 0, L.stream>>>(xv, hv, k0, k0 + N, k0 + 2 * N, L.g.nx, L.g.ny, L.g.nz, L.ph, (real)L.dt, L.bc);
         } else {
             if (hs)
-                k_stage_rhs<real, false, true><<<blocks, threads, 0, L.stream>>>(xv, hv, k0, k0 + N, k0 + 2 * N, L.g.nx, L.g.ny, L.g.nz, L.ph, (real)L.dt, L.bc);
+                k_stage_rhs<real, false, true><<<rgrid, kGX, 0, L.stream>>>(xv, hv, k0, k0 + N, k0 + 2 * N, L.g.nx, L.g.ny, L.g.nz, L.ph, (real)L.dt, L.bc);
             else
-                k_stage_rhs<real, false, false><<<blocks, threads, 0, L.stream>>>(xv, hv, k0, k0 + N, k0 + 2 * N, L.g.nx, L.g.ny, L.g.nz, L.ph, (real)L.dt, L.bc);
+                k_stage_rhs<real, false, false><<<rgrid, kGX, 0, L.stream>>>(xv, hv, k0, k0 + N, k0 + 2 * N, L.g.nx, L.g.ny, L.g.nz, L.ph, (real)L.dt, L.bc);
         }
     }
     CombineArgs<real> c{};
@@ -529,7 +553,7 @@ static cudaError_t launch_generic(const StepLaunch<real>& L) {
     c.replica = L.replica;
     c.sigma = L.sigma;
     c.interval = L.d_interval;
-    k_combine<real><<<blocks, threads, 0, L.stream>>>(c, N);
+    launch_combine<real>(tb.stages, c, N, blocks, threads, L.stream);
     return cudaGetLastError();
 }
 
