@@ -1,0 +1,81 @@
+"""Equilibrium of the full-size 128^3 lattice (J = 1, D = 0.05 along z,
+H = (0, 0, 0.02), lambda = 0.01, FP32, fused RK4 step with the precession
+term) against the GPU checkerboard Metropolis (itself matched to the oracle's
+sweeps) on the same lattice: |M| and E per spin.
+
+The step obeys the precession condition of Sec. III.B, gamma H_eff dt
+~ 6 * 0.04 = 0.24 (at dt = 0.2 the noiseless undamped step no longer
+conserves the energy, see the oracle pin test_precession_step_limit_on_the_lattice),
+and two pulse intervals Delta t = 2 and 0.48 test the pulse condition of
+Sec. III.A: the pulse-noise result is "hotter" than the Boltzmann one by an
+amount that falls with Lambda_N Delta t = 2 lambda T Delta t.  Measured
+(Metropolis: T = 1.0 |M| 0.7048, E -1.9218; T = 1.3 0.5284, -1.4252):
+
+    T    Lambda_N Delta t   |M|       E
+    1.0  0.040              0.70337   -1.91743
+    1.0  0.0096             0.70469   -1.92118
+    1.3  0.052              0.5232    -1.41325
+    1.3  0.0125             0.52674   -1.4223
+
+so the energy bias is about 0.23 Lambda_N Delta t and extrapolates to zero."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import spin_inputs
+
+pytestmark = pytest.mark.gpu
+
+N = 128
+PHYS = dict(J=1.0, D=0.05, H=(0.0, 0.0, 0.02))
+
+
+def _binned(x, nb=20):
+    b = np.array_split(np.asarray(x), nb)
+    m = np.array([v.mean() for v in b])
+    return m.mean(), m.std(ddof=1) / math.sqrt(nb)
+
+
+def _pulse_noise(gpu, T, R):
+    p = gpu.Params(N, N, N, lam=0.01, T=T, dt=0.04, R=R, integrator=gpu.RK4, precision=32, seed=5, **PHYS)
+    lat = gpu.Lattice(p, torch.from_numpy(spin_inputs.aligned_spins(N, N, N)))
+    for _ in range(3):                     # t = 1200: relaxed out of the ordered start
+        lat.step(10000)
+        lat.samples()
+    recs = []
+    for _ in range(8):                     # t = 1600 sampled every Delta t
+        lat.step(5000)
+        recs.append(np.array(lat.samples()))
+    lat.close()
+    rec = np.concatenate(recs)
+    assert len(rec) == 40000 // R
+    return _binned(np.linalg.norm(rec[:, 1:4], axis=1)), _binned(rec[:, 4])
+
+
+def _metropolis(gpu, T):
+    p = gpu.Params(N, N, N, T=T, precision=32, **PHYS)
+    lat = gpu.Lattice(p, torch.from_numpy(spin_inputs.aligned_spins(N, N, N)))
+    gpu.spin_metropolis_sweeps(p, lat.state, 1000, mc_seed=7)
+    m, e = [], []
+    for k in range(300):
+        gpu.spin_metropolis_sweeps(p, lat.state, 10, mc_seed=7, sweep0=1000 + 10 * k)
+        M, E = lat.observables()
+        m.append(float(np.linalg.norm(M)))
+        e.append(E)
+    lat.close()
+    return _binned(m), _binned(e)
+
+
+@pytest.mark.parametrize("T", [1.0, 1.3])
+def test_full_size_equilibrium_matches_metropolis(gpu, T):
+    (m_mc, em_mc), (E_mc, eE_mc) = _metropolis(gpu, T)
+    E_by_R = {}
+    for R, tol_m, tol_E in ((50, 0.01, 0.015), (12, 0.005, 0.005)):
+        (m, em), (E, eE) = _pulse_noise(gpu, T, R)
+        assert abs(m - m_mc) < 5 * math.hypot(em, em_mc) + tol_m, (T, R, m, em, m_mc, em_mc)
+        assert abs(E - E_mc) < 5 * math.hypot(eE, eE_mc) + tol_E, (T, R, E, eE, E_mc, eE_mc)
+        E_by_R[R] = (E, eE)
+    (E50, e50), (E12, e12) = E_by_R[50], E_by_R[12]
+    assert E50 - E12 > 3 * math.hypot(e50, e12), (T, E_by_R)   # the bias falls with Delta t

@@ -232,3 +232,23 @@ def test_slow_equation_lambda_scales_out(orc, k):
     else:
         assert np.max(np.abs(a - b)) < 1e-12
     assert np.allclose(sa[:, 1:], sb[:, 1:], atol=1e-12)
+
+
+def test_precession_step_limit_on_the_lattice(orc):
+    """Sec. III.B: with the precession term the integration step must keep
+    gamma H_eff dt at or below about 0.25, larger steps lose accuracy.  On the
+    simple-cubic lattice the exchange field is up to 6 J, so dt = 0.2 gives
+    gamma H_eff dt ~ 1.2: started from a T = 1.3 Metropolis state, the
+    noiseless, undamped, renormalised RK4 step then changes the energy (an
+    integral of motion at lambda = 0) by more than one J per spin in 200 time
+    units, while dt = 0.04 (gamma H_eff dt ~ 0.24) keeps it within 0.02."""
+    n = 8
+    q = orc.Params(n, n, n, J=1.0, D=0.05, H=(0, 0, 0.02), T=1.3)
+    s, _, _ = orc.metropolis(q, spin_inputs.aligned_spins(n, n, n), 500, mc_seed=3)
+    drift = {}
+    for dt in (0.2, 0.04):
+        p = orc.Params(n, n, n, J=1.0, D=0.05, H=(0, 0, 0.02), lam=0.0, dt=dt, R=10 ** 6)
+        out, _ = orc.run(p, s, int(round(200 / dt)), noise=False)
+        drift[dt] = abs(orc.observables(p, out)[3] - orc.observables(p, s)[3])
+    assert drift[0.04] < 0.02, drift
+    assert drift[0.2] > 1.0, drift
