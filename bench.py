@@ -122,7 +122,9 @@ def _measured_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clock/throttle samples every 200 ms while running."""
+    """nvidia-smi clock/throttle samples every 20 ms; ``stop`` summarises the
+    samples that arrived inside the window marked by ``mark_begin`` /
+    ``mark_end`` (the timed region)."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -131,22 +133,35 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.lines = []
+        self.lines = []          # (arrival time, line)
         self.t = None
+        self.window = (None, None)
 
-    def start(self):
+    def start(self, wait_s: float = 5.0):
+        """Start sampling and wait (up to wait_s) until the first sample has
+        arrived, so that the timed region that follows is covered."""
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "20"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except Exception:
             self.proc = None
+            return
+        t0 = time.perf_counter()
+        while not self.lines and time.perf_counter() - t0 < wait_s and self.proc.poll() is None:
+            time.sleep(0.01)
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def mark_begin(self):
+        self.window = (time.perf_counter(), None)
+
+    def mark_end(self):
+        self.window = (self.window[0], time.perf_counter())
 
     def stop(self):
         if self.proc is None:
@@ -160,7 +175,16 @@ class ClockSampler:
             self.t.join(timeout=2)
         sm, smax, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        b, e = self.window
+        inside = [ln for t, ln in self.lines if b is not None and e is not None and b <= t <= e + 0.05]
+        where = "timed region"
+        if not inside:
+            # a timed region shorter than the sampling period: the samples
+            # nearest to it on either side
+            where = "nearest to the timed region (none inside it)"
+            near = sorted(self.lines, key=lambda q: min(abs(q[0] - (b or 0)), abs(q[0] - (e or 0))))
+            inside = [ln for _, ln in near[:2]]
+        for ln in inside:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -173,12 +197,16 @@ class ClockSampler:
                 if v.lower() == "active":
                     reasons.add(nm)
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "sampled": where}
+
+
+# the sources k_step_patch is compiled from (its own file and the headers it includes)
+PATCH_KERNEL_SOURCES = ("step_patch.cu", "spin_device.cuh", "spin_internal.h")
 
 
 def _kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("spin_device.cuh", "step_kernels.cu", "step_patch.cu"):
+    for f in PATCH_KERNEL_SOURCES:
         h.update(open(os.path.join(ROOT, "paper_1610_04914_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -220,7 +248,8 @@ def cpu_oracle_rate(w, budget_s=15.0, max_steps=10):
     while steps < max_steps:
         s, _ = oracle.run(op, s, 1, n0=steps)
         steps += 1
-        if time.perf_counter() - t0 > budget_s:
+        el = time.perf_counter() - t0
+        if el + el / steps > budget_s:      # the next step would overrun the budget
             break
     dt = time.perf_counter() - t0
     N = nx * ny * nz
@@ -518,6 +547,7 @@ def run_ours(args, ws, rank, local):
     barrier()
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
+    clocks.mark_begin()
     with torch.cuda.stream(stream):
         for k in range(args.steps):
             flush.zero_()
@@ -525,6 +555,7 @@ def run_ours(args, ws, rank, local):
             lat.step(R)
             ev[k][1].record(stream)
     torch.cuda.synchronize()
+    clocks.mark_end()
     barrier()
     wall = time.perf_counter() - wall0
     step_ms = [a.elapsed_time(bb) for a, bb in ev]
@@ -741,7 +772,7 @@ def run_profile_single(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=150)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -145,13 +145,14 @@ def test_fp32_trajectory_16cubed(gpu, orc):
 
 
 @pytest.mark.parametrize("prec", [64, 32])
-@pytest.mark.parametrize("shape", [(16, 16, 16), (5, 7, 3), (1, 1, 1), (2, 2, 2)])
+@pytest.mark.parametrize("shape", [(16, 16, 16), (5, 7, 3), (1, 1, 1), (2, 2, 2), (130, 64, 96)])
 def test_observables(gpu, orc, prec, shape):
     """M and E against the oracle on the same values.  FP64 states: FP64
     arithmetic throughout (1e-13).  FP32 states: per-site terms in FP32 (a bond
     sum of three products of float spins carries at most a few 1e-7 relative
     error, the per-site energy |e_i| < 7 here), accumulated in FP64 per row:
-    bounds 1e-6 for M and 5e-6 for E."""
+    bounds 1e-6 for M and 5e-6 for E.  (130, 64, 96): rows of 130 sites, five
+    columns per lane of which the last is ragged."""
     nx, ny, nz = shape
     p = gpu.Params(nx, ny, nz, J=0.8, D=0.3, H=(0.1, -0.2, 0.3), precision=prec)
     s0 = spin_inputs.random_spins(nx, ny, nz, seed=9)
