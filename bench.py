@@ -286,18 +286,19 @@ def run_reference(args, ws, rank):
     return 0
 
 
-def adjoint_timing(sp, torch, dev):
-    """fwd+adjoint ms/step on the 64^3 differentiation workload: 500 FP32 RK4
+def adjoint_timing(sp, torch, dev, precision=32, steps=None):
+    """fwd+adjoint ms/step on the 64^3 differentiation workload: 500 RK4
     steps with pulses every 10 (recorded, checkpoint every 50), then the
     checkpointed adjoint of E + |M - m*|^2 w.r.t. J, D, H and h_i (FP64
-    accumulation)."""
+    accumulation).  precision 64 is the plain FP64 comparison arm; steps
+    shortens the horizon (accuracy comparison)."""
     w = spin_inputs.WORKLOADS["adjoint64"]
     nx, ny, nz = w["n"]
     p = sp.Params(nx, ny, nz, J=w["J"], D=w["D"], H=w["H"], lam=w["lam"], T=w["T"], dt=w["dt"], R=w["R"],
-                  seed=w["noise_seed"], precision=32)
+                  seed=w["noise_seed"], precision=precision)
     s0 = spin_inputs.random_spins(nx, ny, nz, seed=w["spin_seed"])
     hs = spin_inputs.site_fields(nx, ny, nz, w["field_sigma"], seed=w["noise_seed"])
-    n, K = w["steps"], w["checkpoint"]
+    n, K = (steps or w["steps"]), w["checkpoint"]
     lat = sp.Lattice(p, torch.from_numpy(s0), h_site=torch.from_numpy(hs), device=dev)
     lat.record(K, n)
     torch.cuda.synchronize()
@@ -309,11 +310,36 @@ def adjoint_timing(sp, torch, dev):
     g = lat.backward(dLdM, 1.0, field_grad=True)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
+    gh = g["h"].double().cpu().numpy()
     lat.close()
-    return {"workload": "64^3 FP32 RK4, 500 steps, pulse every 10, checkpoint every 50, loss E + |M - m*|^2",
+    return {"workload": f"64^3 FP{precision} RK4, {n} steps, pulse every 10, checkpoint every 50, "
+                        "loss E + |M - m*|^2",
             "fwd_ms_per_step": 1e3 * (t1 - t0) / n, "adjoint_ms_per_step": 1e3 * (t2 - t1) / n,
             "fwd_plus_adjoint_ms_per_step": 1e3 * (t2 - t0) / n,
-            "grad": {"J": g["J"], "D": g["D"], "H": g["H"]}}
+            "grad": {"J": g["J"], "D": g["D"], "H": g["H"]}, "_gh": gh}
+
+
+def adjoint_vs_fp64(sp, torch, dev, adj32):
+    """The FP32 adjoint against the plain FP64 GPU adjoint on the same
+    workload: time at the full 500-step horizon, and the FP32 gradients'
+    relative error on a 20-step horizon (over 500 steps the pathwise gradient
+    grows with the dynamics' chaos, so FP32 and FP64 runs part for physical
+    reasons, not through the adjoint)."""
+    a64 = adjoint_timing(sp, torch, dev, precision=64)
+    s32 = adjoint_timing(sp, torch, dev, precision=32, steps=20)
+    s64 = adjoint_timing(sp, torch, dev, precision=64, steps=20)
+
+    def rel(a, b):
+        a, b = np.asarray(a, float), np.asarray(b, float)
+        return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+    return {"fp64_fwd_plus_adjoint_ms_per_step": a64["fwd_plus_adjoint_ms_per_step"],
+            "fp64_fwd_ms_per_step": a64["fwd_ms_per_step"], "fp64_adjoint_ms_per_step": a64["adjoint_ms_per_step"],
+            "fp32_speedup": a64["fwd_plus_adjoint_ms_per_step"] / adj32["fwd_plus_adjoint_ms_per_step"],
+            "rel_err_fp32_vs_fp64_20_steps": {"J": rel(s32["grad"]["J"], s64["grad"]["J"]),
+                                              "D": rel(s32["grad"]["D"], s64["grad"]["D"]),
+                                              "H": rel(s32["grad"]["H"], s64["grad"]["H"]),
+                                              "h_i": rel(s32["_gh"], s64["_gh"])}}
 
 
 def batch_timing(sp, torch, dev, flush, stream, hbm_peak, intervals=3):
@@ -343,10 +369,36 @@ def batch_timing(sp, torch, dev, flush, stream, hbm_peak, intervals=3):
     t = sum(a.elapsed_time(c) for a, c in evs) / 1e3
     rate = ntot * p.R * intervals / t
     b.close()
-    return {"workload": "512 replicas, L in {16,24,32,48,64}, T in [0.2,2], FP32 RK4 dt=0.2, pulse every 10",
-            "spins": ntot, "value": rate, "unit": "spin-steps/s", "ms_per_interval": 1e3 * t / intervals,
-            "chunk_planes": b.chunk_planes, "work_items": b.nitems,
-            "hbm_frac_algorithmic": BYTES_PER_SPIN_STEP_FP32 * rate / 1e9 / hbm_peak}
+    out = {"workload": "512 replicas, L in {16,24,32,48,64}, T in [0.2,2], FP32 RK4 dt=0.2, pulse every 10",
+           "spins": ntot, "value": rate, "unit": "spin-steps/s", "ms_per_interval": 1e3 * t / intervals,
+           "chunk_planes": b.chunk_planes, "work_items": b.nitems,
+           "hbm_frac_algorithmic": BYTES_PER_SPIN_STEP_FP32 * rate / 1e9 / hbm_peak}
+    # comparison arms: the same replicas as separate plain lattices, one
+    # interval each, stepped back to back on the stream (FP32: what batching
+    # saves; FP64: the plain FP64 GPU step the batched FP32 form replaces)
+    for prec in (32, 64):
+        lats = []
+        with torch.cuda.stream(stream):
+            for r, (l, tr) in enumerate(zip(L, T)):
+                pr = sp.Params(int(l), int(l), int(l), J=w["J"], D=w["D"], H=w["H"], lam=w["lam"], T=float(tr),
+                               dt=w["dt"], R=w["R"], seed=w["seed"], replica=r, precision=prec)
+                lt = sp.Lattice(pr, torch.from_numpy(states[r]), device=dev, stream=stream)
+                lt.step(pr.R)
+                lats.append(lt)
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for lt in lats:
+                lt.step(p.R)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        out[f"replica_loop_fp{prec}_ms_per_interval"] = e0.elapsed_time(e1)
+        for lt in lats:
+            lt.close()
+        del lats
+    out["batched_speedup_vs_fp64_loop"] = out["replica_loop_fp64_ms_per_interval"] / out["ms_per_interval"]
+    out["batched_speedup_vs_fp32_loop"] = out["replica_loop_fp32_ms_per_interval"] / out["ms_per_interval"]
+    return out
 
 
 def single_spin_timing(sp, torch, stream, alu_peak, blocks_per_sm=10, steps32=20000, steps64=2000):
@@ -595,6 +647,9 @@ def run_ours(args, ws, rank, local):
     d2h = host_out.numel() * host_out.element_size() + 5 * 8
 
     adj = adjoint_timing(sp, torch, dev) if rank == 0 and not args.no_extra else None
+    if adj is not None:
+        adj.pop("_gh")
+        adj["vs_fp64"] = adjoint_vs_fp64(sp, torch, dev, adj)
     bat = batch_timing(sp, torch, dev, flush, stream, hbm_peak) if rank == 0 and not args.no_extra else None
     k256 = kernel_timing_256(sp, torch, dev, flush, stream, hbm_peak) if rank == 0 and not args.no_extra else None
     f64 = fp64_step_timing(sp, torch, dev, flush, stream) if rank == 0 and not args.no_extra else None
