@@ -42,6 +42,28 @@ def random_spins(nx: int, ny: int, nz: int, seed: int, stream: int = 0) -> np.nd
     return s.reshape(3, nz, ny, nx)
 
 
+def random_spins_device(nx: int, ny: int, nz: int, seed: int, device="cuda", chunk_planes: int = 64):
+    """Unit vectors uniform on the sphere drawn directly in device memory as a
+    float32 tensor (3, nz, ny, nx), for lattices too large to draw on the
+    host: z = 2u - 1 and azimuth 2 pi u' from torch's seeded generator on the
+    device, chunk by chunk along z (same recipe as ``random_spins``, another
+    random stream)."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    s = torch.empty((3, nz, ny, nx), dtype=torch.float32, device=device)
+    for z0 in range(0, nz, chunk_planes):
+        z1 = min(nz, z0 + chunk_planes)
+        shape = (z1 - z0, ny, nx)
+        cz = 2.0 * torch.rand(shape, generator=g, device=device, dtype=torch.float64) - 1.0
+        ph = 2.0 * np.pi * torch.rand(shape, generator=g, device=device, dtype=torch.float64)
+        st = torch.sqrt(torch.clamp(1.0 - cz * cz, min=0.0))
+        s[0, z0:z1] = (st * torch.cos(ph)).float()
+        s[1, z0:z1] = (st * torch.sin(ph)).float()
+        s[2, z0:z1] = cz.float()
+    return s
+
+
 def aligned_spins(nx: int, ny: int, nz: int, direction=(0.0, 0.0, 1.0)) -> np.ndarray:
     d = np.asarray(direction, dtype=np.float64)
     d = d / np.linalg.norm(d)

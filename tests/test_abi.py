@@ -58,6 +58,10 @@ def test_validation_without_gpu(lib):
         q = sp.Params(**{**dict(nx=16, ny=16, nz=16), **bad})
         assert L.spin_workspace_size(ctypes.byref(q.c()), ctypes.byref(n)) == B.SPIN_EINVAL
     assert L.spin_workspace_size(None, ctypes.byref(n)) == B.SPIN_EINVAL
+    # the largest lattice: N < 2^31 sites (1290^3 = 2146689000 is accepted)
+    assert L.spin_workspace_size(ctypes.byref(sp.Params(1290, 1290, 1290).c()), ctypes.byref(n)) == 0
+    assert n.value >= 3 * 4 * 1290 ** 3
+    assert L.spin_workspace_size(ctypes.byref(sp.Params(1290, 1290, 1291).c()), ctypes.byref(n)) == B.SPIN_EINVAL
     assert L.spin_step_pulse(None, 1) == B.SPIN_EINVAL
     assert L.spin_strerror(B.SPIN_ENONFINITE).decode().startswith("non-finite")
 
