@@ -233,7 +233,14 @@ __device__ __forceinline__ void patch_iteration(const PatchArgs& a, PRings<S, HS
     const int up = cy0 > 0 ? cy0 - 1 : cy0;                     // row above the first row (clamped at the tile edge)
     const int dn = cy0 + PY < ROWS ? cy0 + PY : cy0 + PY - 1;   // row below the last row
 
-    // 3. stage j on plane t+S-j
+    // 3. stage j on plane t+S-j; the rows above and below for stage j+1 are
+    //    requested from shared memory before stage j's arithmetic
+    f2 nb_up[3], nb_dn[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        nb_up[c] = *reinterpret_cast<const f2*>(shb + c * TILE + up * kRS + cx0);
+        nb_dn[c] = *reinterpret_cast<const f2*>(shb + c * TILE + dn * kRS + cx0);
+    }
 #pragma unroll
     for (int j = 1; j <= S; ++j) {
         // the 2*PY rows of warp w take part in stage j only if they meet the
@@ -242,12 +249,11 @@ __device__ __forceinline__ void patch_iteration(const PatchArgs& a, PRings<S, HS
         const int slot = (P + S - j) & 3;
         const int sm = (slot + 3) & 3, sp = (slot + 1) & 3;
         if (active) {
-            const float* shj = shb + (j - 1) * 3 * TILE;
             f2 cen[PY][3], sum[PY][3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                const f2 row_up = *reinterpret_cast<const f2*>(shj + c * TILE + up * kRS + cx0);
-                const f2 row_dn = *reinterpret_cast<const f2*>(shj + c * TILE + dn * kRS + cx0);
+                const f2 row_up = nb_up[c];
+                const f2 row_dn = nb_dn[c];
 #pragma unroll
                 for (int rr = 0; rr < PY; ++rr) {
                     const f2 C = (j == 1) ? r.s[slot][rr][c] : r.x[j - 2][slot][rr][c];
@@ -266,6 +272,14 @@ __device__ __forceinline__ void patch_iteration(const PatchArgs& a, PRings<S, HS
                     // value the previous stage produced in this iteration
                     sum[rr][c] = add2(add2(add2(xs, add2(ym, yp)), ZM), ZP);
                     cen[rr][c] = C;
+                }
+            }
+            if (j < S) {
+                const float* shn = shb + j * 3 * TILE;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    nb_up[c] = *reinterpret_cast<const f2*>(shn + c * TILE + up * kRS + cx0);
+                    nb_dn[c] = *reinterpret_cast<const f2*>(shn + c * TILE + dn * kRS + cx0);
                 }
             }
 #pragma unroll
