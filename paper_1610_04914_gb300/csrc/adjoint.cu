@@ -607,10 +607,12 @@ cudaError_t adjoint_run(const AdjointRun<real>& A) {
     for (int sgi = nseg - 1; sgi >= 0; --sgi) {
         const long long start = A.n0 + (long long)sgi * A.K;
         const int seglen = (int)std::min<long long>(A.K, A.n_end - start);
-        // restore checkpoint and recompute the segment with the forward kernels
+        // restore checkpoint and recompute the segment with the forward kernels;
+        // the transposed steps read the states 0 .. seglen-1 of the segment,
+        // so its last state is not recomputed
         e = cudaMemcpyAsync(seg, A.store + (size_t)sgi * len, compb, cudaMemcpyDeviceToDevice, st);
         if (e != cudaSuccess) return e;
-        for (int m = 1; m <= seglen; ++m) {
+        for (int m = 1; m < seglen; ++m) {
             const long long n = start + m;
             const bool pul = A.noise && (n % A.R) == (A.R / 2);
             if (pul) {
