@@ -186,7 +186,12 @@ int spin_record_end(spin_lattice* h);
  * stages of Eq. (LLL) (tableaus of the paper's Appendix), renormalisation and
  * the pulse rotation of Eq. (s_rotation) (transposed: rotation by -phi).
  * The backward pass restores each checkpoint, recomputes its K steps with
- * the forward kernels and runs the transposed steps backwards.
+ * the forward kernels and runs the transposed steps backwards.  For FP32
+ * states with a chain tableau (RK4, RK2 midpoint, Heun) on the fused path the
+ * recomputing steps also write every stage's input and increment, which the
+ * transposed steps read instead of recomputing them; the workspace then holds
+ * (2 x stages - 1) x K extra arrays of 3N values (taken only while they come
+ * to at most 8 GiB; otherwise the stages are recomputed per step).
  *   dLdM, dLdE   host seeds of the loss
  *   workspace    device, >= spin_backward_workspace_size(p, K) bytes, 256-aligned
  *   gJ, gD, gH   host outputs: dL/dJ, dL/dD, dL/dH (3), including the explicit

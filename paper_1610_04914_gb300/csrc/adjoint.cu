@@ -448,10 +448,21 @@ int grid_for(long long n) { return (int)std::max<long long>(1, std::min<long lon
 
 int adjoint_blocks(Geom g) { return grid_for(g.N()); }
 
-size_t adjoint_workspace_bytes(const Geom& g, int elt, int stages, int K) {
+constexpr size_t kStageStoreMax = (size_t)8 << 30;   // bytes of stage storage at most
+
+bool adjoint_stores_stages(const Geom& g, int elt, const Tableau& tb, int path, int K) {
+    if (elt != 4 || !tb.chain || path == 1 || !(tb.stages == 2 || tb.stages == 4)) return false;
+    const size_t comp = ((size_t)3 * (size_t)g.N() * 4 + 255) / 256 * 256;
+    return comp * (size_t)(2 * tb.stages - 1) * (size_t)K <= kStageStoreMax;
+}
+
+size_t adjoint_workspace_bytes(const Geom& g, int elt, const Tableau& tb, int path, int K) {
+    const int stages = tb.stages;
     const size_t comp = (size_t)3 * (size_t)g.N() * (size_t)elt;
     auto al = [](size_t v) { return (v + 255) / 256 * 256; };
     size_t b = 0;
+    if (adjoint_stores_stages(g, elt, tb, path, K))
+        b += al(comp) * (size_t)(2 * stages - 1) * (size_t)K;   // X_j (j >= 2) and K_j of every step of a segment
     b += al(comp) * (size_t)(K + 1);     // segment states
     b += al(comp) * (size_t)stages * 3;  // X_j, K_j, lam_K_j
     b += al(comp) * 7;                   // y, lam, w and u (two pairs), segment field gradient
@@ -565,6 +576,17 @@ cudaError_t adjoint_run(const AdjointRun<real>& A) {
     double* acc = reinterpret_cast<double*>(ws + off);
     off += al(sizeof(double) * 8);
     long long* kslot = reinterpret_cast<long long*>(ws + off);
+    off += al(sizeof(long long));
+    // stage storage of a segment (A.store_stages): for step m of the segment
+    // (slot m-1) the inputs X_2..X_S and the increments K_1..K_S
+    const bool stored = A.store_stages != 0;
+    char* sbase = ws + off;
+    auto stage_x = [&](int j, int m) {   // X_j, j = 2..S (0-based stage index j-1 >= 1)
+        return reinterpret_cast<real*>(sbase + ((size_t)(m - 1) * (2 * S - 1) + (size_t)(j - 2)) * al(compb));
+    };
+    auto stage_k = [&](int j, int m) {   // K_j, j = 1..S
+        return reinterpret_cast<real*>(sbase + ((size_t)(m - 1) * (2 * S - 1) + (size_t)(S - 1) + (size_t)(j - 1)) * al(compb));
+    };
     cudaStream_t st = A.stream;
     const real J = (real)A.J, twoD = (real)(2.0 * A.D), H0 = (real)A.H[0], H1 = (real)A.H[1], H2 = (real)A.H[2];
     const real lamb = (real)A.lambda, dt = (real)A.dt;
@@ -609,10 +631,11 @@ cudaError_t adjoint_run(const AdjointRun<real>& A) {
         const int seglen = (int)std::min<long long>(A.K, A.n_end - start);
         // restore checkpoint and recompute the segment with the forward kernels;
         // the transposed steps read the states 0 .. seglen-1 of the segment,
-        // so its last state is not recomputed
+        // so its last state is not recomputed unless the steps also store
+        // their stages (then every step of the segment runs)
         e = cudaMemcpyAsync(seg, A.store + (size_t)sgi * len, compb, cudaMemcpyDeviceToDevice, st);
         if (e != cudaSuccess) return e;
-        for (int m = 1; m < seglen; ++m) {
+        for (int m = 1; m < seglen + (stored ? 1 : 0); ++m) {
             const long long n = start + m;
             const bool pul = A.noise && (n % A.R) == (A.R / 2);
             if (pul) {
@@ -629,6 +652,13 @@ cudaError_t adjoint_run(const AdjointRun<real>& A) {
             L.pulse = pul ? 1 : 0;
             L.d_interval = kslot;
             L.stream = st;
+            if (stored) {
+                for (int j = 1; j <= S; ++j)
+                    for (int c = 0; c < 3; ++c) {
+                        L.st_k[j - 1][c] = stage_k(j, m) + c * N;
+                        if (j >= 2) L.st_x[j - 2][c] = stage_x(j, m) + c * N;
+                    }
+            }
             e = launch_step<real>(L);
             if (e != cudaSuccess) return e;
         }
@@ -639,7 +669,10 @@ cudaError_t adjoint_run(const AdjointRun<real>& A) {
             const real* s = seg + (size_t)(m - 1) * len;
             // stages X_j and K_j = dt f(X_j); the first stage's input is s itself
             const real* Xs[6];
-            for (int j = 0; j < S; ++j) {
+            real* Kp[6];
+            for (int j = 0; j < S; ++j) Kp[j] = stored ? stage_k(j + 1, m) : Kst[j];
+            for (int j = 0; j < S && stored; ++j) Xs[j] = j == 0 ? s : stage_x(j + 1, m);
+            for (int j = 0; j < S && !stored; ++j) {
                 if (j == 0) {
                     Xs[0] = s;
                 } else {
@@ -663,7 +696,7 @@ cudaError_t adjoint_run(const AdjointRun<real>& A) {
             ta.lam = lam;
             ta.s = s;
             for (int l = 0; l < S; ++l) {
-                ta.yc.K[l] = Kst[l];
+                ta.yc.K[l] = Kp[l];
                 ta.yc.coef[l] = (real)tb.b[l];
             }
             for (int j = 0; j < S; ++j) {

@@ -257,6 +257,7 @@ int backward_t(spin_lattice* h, const double dLdM[3], double dLdE, void* ws, dou
     A.precession = h->p.precession;
     A.renorm = h->p.renorm;
     A.bc = h->p.bc;
+    A.store_stages = adjoint_stores_stages(h->g, (int)sizeof(real), h->tab, h->p.path, h->rec_K) ? 1 : 0;
     A.seed = h->p.seed;
     A.replica = (uint64_t)h->p.replica;
     A.sigma = std::sqrt(2.0 * h->p.lambda * h->p.T * h->p.steps_per_pulse * std::fabs(h->p.dt));
@@ -489,7 +490,7 @@ int spin_backward_workspace_size(const spin_params* p, int32_t K, size_t* bytes)
     int v = validate(p);
     if (v != SPIN_OK) return v;
     const Tableau tb = tableau_for(p->integrator);
-    *bytes = adjoint_workspace_bytes(Geom{p->nx, p->ny, p->nz}, p->precision == 64 ? 8 : 4, tb.stages, K);
+    *bytes = adjoint_workspace_bytes(Geom{p->nx, p->ny, p->nz}, p->precision == 64 ? 8 : 4, tb, p->path, K);
     return SPIN_OK;
 }
 

@@ -50,6 +50,11 @@ struct StepLaunch {
     cudaStream_t stream;
     int force_generic;
     int bc;                // 0 periodic, 1 free boundaries
+    // FP32 fused path only: if st_k[0][0] is set, the step also writes the
+    // stage inputs X_j (j = 2..S, st_x[j-2]) and increments K_j = dt f(X_j)
+    // (j = 1..S, st_k[j-1]) of every site, component arrays of 3 x N
+    real* st_x[3][3];
+    real* st_k[4][3];
 };
 
 template <typename real>
@@ -119,6 +124,7 @@ struct AdjointRun {
     int K;                   // checkpoint interval (steps)
     long long n0, n_end;     // recorded range: states n0 .. n_end
     int R, noise, precession, renorm, bc;
+    int store_stages;        // stage storage of the segment (adjoint_stores_stages)
     uint64_t seed, replica;
     double sigma, J, D, H[3], lambda, dt;
     const real* h_site;      // component-major 3N or null
@@ -135,7 +141,12 @@ struct AdjointRun {
     double* g_h;             // device FP64 3N or null
     real* g_s0;              // device 3N or null
 };
-size_t adjoint_workspace_bytes(const Geom& g, int elt, int stages, int K);
+// Whether the adjoint keeps each checkpoint segment's stage inputs and
+// increments from the recomputation (FP32 fused-step path, chain tableaus of 2
+// or 4 stages, at most 8 GiB of stage storage) instead of recomputing the
+// stages in every transposed step.
+bool adjoint_stores_stages(const Geom& g, int elt, const Tableau& tb, int path, int K);
+size_t adjoint_workspace_bytes(const Geom& g, int elt, const Tableau& tb, int path, int K);
 template <typename real>
 cudaError_t adjoint_run(const AdjointRun<real>& A);
 

@@ -69,6 +69,13 @@ struct PatchArgs {
     int bc;            // 1: free boundaries (outside columns and planes read as zero spins)
     int pair8;         // 1: each thread's column pair is one aligned 8-byte word of every input plane
     int pair8out;      // 1: the same for the output planes
+    // stage store (STORE variant, for the adjoint's recomputation): at the
+    // output sites, the stage inputs X_j (j = 2..S, stx[j-2]) and the stage
+    // increments K_j = dt f(X_j) (j = 1..S, stk[j-1]), component arrays in the
+    // lattice's layout
+    float* stx[3][3];
+    float* stk[4][3];
+    float dt;
 };
 
 // A column pair (2m, 2m+1) is contiguous in a row of even length and never
@@ -168,7 +175,7 @@ __device__ __forceinline__ void issue_plane(const PatchArgs& a, float* stg, cons
     cp_async_commit();
 }
 
-template <int S, bool PREC, bool HSITE, bool PULSE, int P>
+template <int S, bool PREC, bool HSITE, bool PULSE, bool STORE, int P>
 __device__ __forceinline__ void patch_iteration(const PatchArgs& a, PRings<S, HSITE>& r, float* __restrict__ sh,
                                                 float* __restrict__ stg, PThread<PatchShape<S>::PY>& th, int i,
                                                 int t0, int z0, long long k, int tid) {
@@ -312,6 +319,24 @@ __device__ __forceinline__ void patch_iteration(const PatchArgs& a, PRings<S, HS
                     f[1] = mul2(sp2(-a.lambda), by);
                     f[2] = mul2(sp2(-a.lambda), bz);
                 }
+                if (STORE) {
+                    // stage input and increment of plane t+S-j at the output sites
+                    const int pz = t + S - j;
+                    if (pz >= z0 && pz < z0 + a.tz && pz < a.nz) {
+                        const long long base = (long long)pz * th.plane;
+#pragma unroll
+                        for (int e = 0; e < 2; ++e) {
+                            if (!th.out[rr][e]) continue;
+                            const long long site = base + th.col[rr][e];
+#pragma unroll
+                            for (int c = 0; c < 3; ++c) {
+                                const f2 kk = mul2(sp2(a.dt), f[c]);
+                                a.stk[j - 1][c][site] = e == 0 ? kk.x : kk.y;
+                                if (j >= 2) a.stx[j >= 2 ? j - 2 : 0][c][site] = e == 0 ? cen[rr][c].x : cen[rr][c].y;
+                            }
+                        }
+                    }
+                }
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     if (j == 1)
@@ -362,7 +387,7 @@ __device__ __forceinline__ void patch_iteration(const PatchArgs& a, PRings<S, HS
 }
 
 // One CTA's tile: columns (bx, by) of the x-y tiling, z chunk bz.
-template <int S, bool PREC, bool HSITE, bool PULSE>
+template <int S, bool PREC, bool HSITE, bool PULSE, bool STORE>
 __device__ __forceinline__ void patch_tile(const PatchArgs& a, int bx, int by, int bz, float* __restrict__ sh) {
     constexpr int PY = PatchShape<S>::PY, ROWS = PatchShape<S>::PY * PatchShape<S>::TY;
     float* stg = sh + 2 * S * 3 * ROWS * kRS;
@@ -430,22 +455,31 @@ __device__ __forceinline__ void patch_tile(const PatchArgs& a, int bx, int by, i
     th.gz_field = wrapi(t0 + S - 1, a.nz);
     int i = 0;
     for (; i + 4 <= a.n_iter; i += 4) {
-        patch_iteration<S, PREC, HSITE, PULSE, 0>(a, r, sh, stg, th, i + 0, t0, z0, k, tid);
-        patch_iteration<S, PREC, HSITE, PULSE, 1>(a, r, sh, stg, th, i + 1, t0, z0, k, tid);
-        patch_iteration<S, PREC, HSITE, PULSE, 2>(a, r, sh, stg, th, i + 2, t0, z0, k, tid);
-        patch_iteration<S, PREC, HSITE, PULSE, 3>(a, r, sh, stg, th, i + 3, t0, z0, k, tid);
+        patch_iteration<S, PREC, HSITE, PULSE, STORE, 0>(a, r, sh, stg, th, i + 0, t0, z0, k, tid);
+        patch_iteration<S, PREC, HSITE, PULSE, STORE, 1>(a, r, sh, stg, th, i + 1, t0, z0, k, tid);
+        patch_iteration<S, PREC, HSITE, PULSE, STORE, 2>(a, r, sh, stg, th, i + 2, t0, z0, k, tid);
+        patch_iteration<S, PREC, HSITE, PULSE, STORE, 3>(a, r, sh, stg, th, i + 3, t0, z0, k, tid);
     }
-    if (i < a.n_iter) patch_iteration<S, PREC, HSITE, PULSE, 0>(a, r, sh, stg, th, i + 0, t0, z0, k, tid);
-    if (i + 1 < a.n_iter) patch_iteration<S, PREC, HSITE, PULSE, 1>(a, r, sh, stg, th, i + 1, t0, z0, k, tid);
-    if (i + 2 < a.n_iter) patch_iteration<S, PREC, HSITE, PULSE, 2>(a, r, sh, stg, th, i + 2, t0, z0, k, tid);
+    if (i < a.n_iter) patch_iteration<S, PREC, HSITE, PULSE, STORE, 0>(a, r, sh, stg, th, i + 0, t0, z0, k, tid);
+    if (i + 1 < a.n_iter) patch_iteration<S, PREC, HSITE, PULSE, STORE, 1>(a, r, sh, stg, th, i + 1, t0, z0, k, tid);
+    if (i + 2 < a.n_iter) patch_iteration<S, PREC, HSITE, PULSE, STORE, 2>(a, r, sh, stg, th, i + 2, t0, z0, k, tid);
     cp_async_wait<0>();   // no copy may land in shared memory after the tile is done
 }
 
 template <int S, bool PREC, bool HSITE, bool PULSE>
 __global__ void __launch_bounds__(kPT* PatchShape<S>::TY, 1) k_step_patch(PatchArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    patch_tile<S, PREC, HSITE, PULSE>(a, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z,
-                                      reinterpret_cast<float*>(smem_raw));
+    patch_tile<S, PREC, HSITE, PULSE, false>(a, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z,
+                                             reinterpret_cast<float*>(smem_raw));
+}
+
+// The same step that also writes every stage's input and increment at the
+// output sites (the adjoint reads them instead of recomputing the stages).
+template <int S, bool PREC, bool HSITE>
+__global__ void __launch_bounds__(kPT* PatchShape<S>::TY, 1) k_step_patch_store(PatchArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    patch_tile<S, PREC, HSITE, false, true>(a, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z,
+                                            reinterpret_cast<float*>(smem_raw));
 }
 
 // Batched replicas: one CTA per work item (replica, x tile, y tile, z chunk)
@@ -472,7 +506,7 @@ __global__ void __launch_bounds__(kPT* PatchShape<S>::TY, 1)
     a.n_iter = rp.tz + 2 * S - 2;
     a.sigma = rp.sigma;
     a.replica = (uint64_t)it.rep;
-    patch_tile<S, PREC, false, PULSE>(a, it.bx, it.by, it.bz, reinterpret_cast<float*>(smem_raw));
+    patch_tile<S, PREC, false, PULSE, false>(a, it.bx, it.by, it.bz, reinterpret_cast<float*>(smem_raw));
 }
 
 template <int S, bool PREC, bool HSITE, bool PULSE>
@@ -489,6 +523,30 @@ cudaError_t patch_launch(const PatchArgs& a, dim3 grid, cudaStream_t st, bool pr
                                     (int)smem);
     k_step_patch<S, PREC, HSITE, PULSE><<<grid, dim3(kPT, PatchShape<S>::TY), smem, st>>>(a);
     return cudaGetLastError();
+}
+
+template <int S, bool PREC, bool HSITE>
+cudaError_t patch_store_launch(const PatchArgs& a, dim3 grid, cudaStream_t st, bool prepare) {
+    const size_t smem = patch_smem<S, PREC, HSITE, false>();
+    if (prepare)
+        return cudaFuncSetAttribute(k_step_patch_store<S, PREC, HSITE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem);
+    k_step_patch_store<S, PREC, HSITE><<<grid, dim3(kPT, PatchShape<S>::TY), smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int S>
+cudaError_t patch_store_dispatch(const PatchArgs& a, dim3 grid, cudaStream_t st, bool prec, bool hs, bool prepare) {
+    if (prepare) {
+        cudaError_t e;
+        if ((e = patch_store_launch<S, true, false>(a, grid, st, true)) != cudaSuccess) return e;
+        if ((e = patch_store_launch<S, true, true>(a, grid, st, true)) != cudaSuccess) return e;
+        if ((e = patch_store_launch<S, false, false>(a, grid, st, true)) != cudaSuccess) return e;
+        return patch_store_launch<S, false, true>(a, grid, st, true);
+    }
+    if (prec) return hs ? patch_store_launch<S, true, true>(a, grid, st, false)
+                        : patch_store_launch<S, true, false>(a, grid, st, false);
+    return hs ? patch_store_launch<S, false, true>(a, grid, st, false) : patch_store_launch<S, false, false>(a, grid, st, false);
 }
 
 template <int S>
@@ -649,7 +707,11 @@ cudaError_t prepare_patch_kernels() {
     PatchArgs a{};
     cudaError_t e = patch_dispatch<4>(a, dim3(1), 0, false, false, false, true);
     if (e != cudaSuccess) return e;
-    return patch_dispatch<2>(a, dim3(1), 0, false, false, false, true);
+    e = patch_dispatch<2>(a, dim3(1), 0, false, false, false, true);
+    if (e != cudaSuccess) return e;
+    e = patch_store_dispatch<4>(a, dim3(1), 0, false, false, true);
+    if (e != cudaSuccess) return e;
+    return patch_store_dispatch<2>(a, dim3(1), 0, false, false, true);
 }
 
 cudaError_t launch_step_patch(const StepLaunch<float>& L) {
@@ -681,8 +743,20 @@ cudaError_t launch_step_patch(const StepLaunch<float>& L) {
     dim3 grid(tiles_x, tiles_y, (L.g.nz + zc - 1) / zc);
     const bool hs = L.hs[0] != nullptr;
     const bool prec = L.precession != 0;
-    cudaError_t e = S == 4 ? patch_dispatch<4>(a, grid, L.stream, prec, hs, false, false)
-                           : patch_dispatch<2>(a, grid, L.stream, prec, hs, false, false);
+    cudaError_t e;
+    if (L.st_k[0][0]) {
+        for (int j = 0; j < S; ++j)
+            for (int c = 0; c < 3; ++c) {
+                a.stk[j][c] = L.st_k[j][c];
+                if (j + 1 < S) a.stx[j][c] = L.st_x[j][c];
+            }
+        a.dt = (float)L.dt;
+        e = S == 4 ? patch_store_dispatch<4>(a, grid, L.stream, prec, hs, false)
+                   : patch_store_dispatch<2>(a, grid, L.stream, prec, hs, false);
+    } else {
+        e = S == 4 ? patch_dispatch<4>(a, grid, L.stream, prec, hs, false, false)
+                   : patch_dispatch<2>(a, grid, L.stream, prec, hs, false, false);
+    }
     if (e != cudaSuccess || !L.pulse) return e;
     const long long N = L.g.N();
     const int blocks = (int)std::max<long long>(1, std::min<long long>((N + 255) / 256, 152LL * 8));
