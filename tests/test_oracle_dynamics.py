@@ -132,6 +132,25 @@ def test_precession_conserves_energy_and_sz(orc):
     assert drifts[0] / drifts[1] > 10.0
 
 
+def test_rk5_energy_drift_order(orc):
+    """lambda = 0: Butcher's RK5 (Appendix) conserves the energy to order 5 —
+    the drift over 2 time units falls ~2^5 per halving of dt once dt is small
+    (measured 28.5 from dt = 0.05 to 0.025) and lies far below RK4's at the
+    same dt (1.1e-7 against 7.6e-6 at dt = 0.05)."""
+    shape = (6, 5, 4)
+    s0 = spin_inputs.random_spins(*shape, seed=3)
+
+    def drift(integrator, dt):
+        p = orc.Params(*shape, J=1.0, D=0.4, H=(0, 0, 0.3), lam=0.0, dt=dt, R=10 ** 6, renorm=0,
+                       integrator=integrator)
+        out, _ = orc.run(p, s0, int(round(2.0 / dt)), noise=False)
+        return abs(orc.observables(p, out)[3] - orc.observables(p, s0)[3])
+
+    d5 = [drift(orc.RK5_BUTCHER, dt) for dt in (0.05, 0.025)]
+    assert d5[0] / d5[1] > 20.0, d5
+    assert d5[0] < drift(orc.RK4, 0.05) / 20.0, d5
+
+
 def test_isotropic_exchange_rigid_rotation(orc):
     """D = 0, lambda = 0: internal exchange torques cancel pairwise, so
     dM/dt = M x H and M rotates rigidly about H by -|H| t."""
