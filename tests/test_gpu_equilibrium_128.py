@@ -9,15 +9,19 @@ conserves the energy, see the oracle pin test_precession_step_limit_on_the_latti
 and two pulse intervals Delta t = 2 and 0.48 test the pulse condition of
 Sec. III.A: the pulse-noise result is "hotter" than the Boltzmann one by an
 amount that falls with Lambda_N Delta t = 2 lambda T Delta t.  Measured
-(Metropolis: T = 1.0 |M| 0.7048, E -1.9218; T = 1.3 0.5284, -1.4252):
+(Metropolis: T = 0.5 |M| 0.87564, E -2.54394; T = 1.0 0.7048, -1.9218;
+T = 1.3 0.5284, -1.4252):
 
     T    Lambda_N Delta t   |M|       E
+    0.5  0.020              0.87564   -2.54413
+    0.5  0.0048             0.87559   -2.54422
     1.0  0.040              0.70337   -1.91743
     1.0  0.0096             0.70469   -1.92118
     1.3  0.052              0.5232    -1.41325
     1.3  0.0125             0.52674   -1.4223
 
-so the energy bias is about 0.23 Lambda_N Delta t and extrapolates to zero."""
+so the energy bias is about 0.23 Lambda_N Delta t at T = 1.3 and extrapolates
+to zero; at T = 0.5 it is below the statistical resolution."""
 import math
 
 import numpy as np
@@ -68,7 +72,7 @@ def _metropolis(gpu, T):
     return _binned(m), _binned(e)
 
 
-@pytest.mark.parametrize("T", [1.0, 1.3])
+@pytest.mark.parametrize("T", [0.5, 1.0, 1.3])
 def test_full_size_equilibrium_matches_metropolis(gpu, T):
     (m_mc, em_mc), (E_mc, eE_mc) = _metropolis(gpu, T)
     E_by_R = {}
@@ -78,4 +82,5 @@ def test_full_size_equilibrium_matches_metropolis(gpu, T):
         assert abs(E - E_mc) < 5 * math.hypot(eE, eE_mc) + tol_E, (T, R, E, eE, E_mc, eE_mc)
         E_by_R[R] = (E, eE)
     (E50, e50), (E12, e12) = E_by_R[50], E_by_R[12]
-    assert E50 - E12 > 3 * math.hypot(e50, e12), (T, E_by_R)   # the bias falls with Delta t
+    if T >= 1.0:   # at T = 0.5 (Lambda_N Delta t <= 0.02) the bias is below the statistical resolution
+        assert E50 - E12 > 3 * math.hypot(e50, e12), (T, E_by_R)   # the bias falls with Delta t
