@@ -198,10 +198,11 @@ int spin_record_end(spin_lattice* h);
  *                dependence of E(s_n) on the parameters
  *   g_h_site     nullable device FP64 array of 3N: dL/dh_i (component-major)
  *   g_s0         nullable device array of 3N (state type): dL/ds_{n0}
- * Parameter gradients accumulate in FP64 over sites, stages and steps; the
- * terms of one warp (32 sites) and, for dL/dh_i, the stage terms of one
- * checkpoint segment are first summed in the state precision.  The adjoint
- * state is kept in the state precision.  Synchronises the stream.
+ * Parameter gradients accumulate in FP64: every site's term of every stage of
+ * every step is formed in the state precision and added in FP64 (dL/dh_i
+ * straight into g_h_site; dL/dJ, dL/dD, dL/dH through FP64 per-thread sums
+ * reduced in FP64).  The adjoint state is kept in the state precision.
+ * Synchronises the stream.
  * Errors: SPIN_EINVAL (no recording, range mismatch), SPIN_ENOSPACE, SPIN_ECUDA.
  */
 int spin_backward_workspace_size(const spin_params* p, int32_t K, size_t* bytes);
@@ -376,6 +377,8 @@ int spin_metropolis_color(const spin_params* p, void* s, const void* h_site, uin
  *   sx, sy, sz  device arrays of N = nx*ny*nz elements (x fastest)
  *   h_site      nullable, device array of 3N elements (x block, y, z)
  *   J, D, H     as in spin_params (H: host array of 3 doubles)
+ *   bc          0 periodic, 1 free boundaries (no bond across a face), as
+ *               spin_params.bc
  *   out5        DEVICE array of 5 doubles receiving (M_x, M_y, M_z, E, number
  *               of non-finite spins); written asynchronously on cuda_stream.
  * Scratch: one 5-double record per reduction block lives in a file-scope
@@ -383,19 +386,22 @@ int spin_metropolis_color(const spin_params* p, void* s, const void* h_site, uin
  * loads the library holds it until the process exits.  All calls share it and
  * it keeps the last call's contents; each call overwrites every record it
  * reads, so nothing needs clearing, but calls that overlap on the GPU (two
- * streams, or two host threads) race on it and must be serialised.  The
- * first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any CUDA
- * stream capture.  Lattices of more than SPIN_NOALLOC_MAX_SITES sites are
+ * streams, or two host threads) race on it and must be serialised.  Outside
+ * stream capture every call looks up the array's device address on the
+ * current device; a call on a stream that is being captured reuses the
+ * address that the last uncaptured call on that device found, so make one
+ * uncaptured call on each device before capturing one.  cudaDeviceReset
+ * reloads the library's module, so after it make one uncaptured call again
+ * before any capture.  Lattices of more than SPIN_NOALLOC_MAX_SITES sites are
  * rejected with SPIN_EINVAL.
- * Errors: SPIN_EINVAL (null pointers, precision, sizes < 1 or beyond the
- * maximum), SPIN_ECUDA.
+ * Errors: SPIN_EINVAL (null pointers, precision, bc, sizes < 1 or beyond the
+ * maximum, a capture before any uncaptured call on the device), SPIN_ECUDA.
  */
 #define SPIN_NOALLOC_MAX_BLOCKS 1024
 #define SPIN_NOALLOC_MAX_SITES 2147483647LL
 int spin_observables_noalloc(int32_t precision, const void* sx, const void* sy, const void* sz,
                              const void* h_site, int32_t nx, int32_t ny, int32_t nz, double J,
-                             double D, const double H[3], double* out5, void* cuda_stream);
+                             double D, const double H[3], int32_t bc, double* out5, void* cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -26,6 +26,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "spin_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
 
 RK4, RK5_BUTCHER, RK2_MIDPOINT, HEUN = 0, 1, 2, 3
 
@@ -39,6 +40,21 @@ def build(force: bool = False) -> str:
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB)
     return _LIB
+
+
+def build_omp(force: bool = False):
+    """The same source compiled with -fopenmp into liboracle_omp.so: its
+    whole-lattice loops run on all host cores with unchanged per-site
+    arithmetic.  Returns the path, or None if the compiler has no OpenMP."""
+    if force or not os.path.exists(_LIB_OMP) or os.path.getmtime(_LIB_OMP) < os.path.getmtime(_SRC):
+        tmp = _LIB_OMP + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            return None
+        os.replace(tmp, _LIB_OMP)
+    return _LIB_OMP
 
 
 class _Params(ctypes.Structure):
@@ -85,12 +101,26 @@ class Params:
 
 
 _lib = None
+_lib_omp = None
 
 
-def lib():
-    global _lib
+def lib(threads: bool = False):
+    """The serial build (default) or, with threads=True, the OpenMP build."""
+    global _lib, _lib_omp
+    if threads:
+        if _lib_omp is None:
+            path = build_omp()
+            if path is None:
+                raise RuntimeError("gcc could not build the OpenMP oracle")
+            _lib_omp = _declare(ctypes.CDLL(path))
+        return _lib_omp
     if _lib is None:
-        L = ctypes.CDLL(build())
+        _lib = _declare(ctypes.CDLL(build()))
+    return _lib
+
+
+def _declare(L):
+    if True:
         P = ctypes.POINTER
         d, u64, i64 = ctypes.c_double, ctypes.c_uint64, ctypes.c_int64
         L.orc_philox4x64.argtypes = [P(u64), P(u64), P(u64)]
@@ -121,8 +151,13 @@ def lib():
         L.orc_step_vjp.argtypes = [P(_Params), P(d), P(d), ctypes.c_int, i64, P(d), P(d), P(d), P(d), P(d)]
         L.orc_adjoint.argtypes = [P(_Params), P(d), P(d), i64, i64, ctypes.c_int, P(d), d, P(d), P(d), P(d),
                                   P(d), P(d)]
-        _lib = L
-    return _lib
+    return L
+
+
+def omp_threads() -> int:
+    """Threads the OpenMP build uses (OMP_NUM_THREADS, else all host cores)."""
+    v = os.environ.get("OMP_NUM_THREADS")
+    return int(v) if v and v.isdigit() and int(v) > 0 else (os.cpu_count() or 1)
 
 
 def _dp(a):
@@ -234,16 +269,17 @@ def observables(p: Params, s, h_site=None) -> np.ndarray:
 NOISE_NONE, NOISE_PULSE, NOISE_RECT = 0, 1, 2
 
 
-def run(p: Params, s, nsteps: int, n0: int = 0, h_site=None, noise=True):
+def run(p: Params, s, nsteps: int, n0: int = 0, h_site=None, noise=True, threads: bool = False):
     """Advance nsteps from completed step n0.  Returns (state, samples) with
     samples rows (n, M_x, M_y, M_z, E) taken after steps with n mod R == 0.
     noise: False/0 none, True/1 the pulses (Eq. (phi_n)), 2 rectangular noise
-    (Eq. (zeta_n), needs the precession term)."""
+    (Eq. (zeta_n), needs the precession term).  threads: run the OpenMP build
+    (same per-site arithmetic on all host cores)."""
     a = _state(p, s)
     hs = _field(p, h_site)
     cap = nsteps // max(p.R, 1) + 2
     smp = np.zeros((cap, 5))
-    ns = lib().orc_run(ctypes.byref(p.c()), _dp(a), _dp(hs), n0, nsteps, int(noise), _dp(smp), cap)
+    ns = lib(threads).orc_run(ctypes.byref(p.c()), _dp(a), _dp(hs), n0, nsteps, int(noise), _dp(smp), cap)
     if ns < 0:
         raise ValueError("rectangular noise needs the precession term (precession=1)")
     return a, smp[:ns]

@@ -85,7 +85,7 @@ def load(path: str = LIB_PATH):
     L.spin_last_error.restype = ctypes.c_char_p
     L.spin_noise_draw.argtypes = [u64, i64, i64, i64, i32, vp, vp, vp]
     d = ctypes.c_double
-    L.spin_observables_noalloc.argtypes = [i32, vp, vp, vp, vp, i32, i32, i32, d, d, P(d), vp, vp]
+    L.spin_observables_noalloc.argtypes = [i32, vp, vp, vp, vp, i32, i32, i32, d, d, P(d), i32, vp, vp]
     L.spin_record_store_size.argtypes = [P(spin_params), i32, i64, P(sz)]
     L.spin_record_begin.argtypes = [vp, i32, i64, vp, sz]
     L.spin_record_end.argtypes = [vp]

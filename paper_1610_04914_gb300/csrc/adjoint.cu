@@ -3,9 +3,10 @@
 // the forward run stores the state every K steps; the backward pass restores
 // each checkpoint, recomputes its K states with the forward kernels, and runs
 // the transposed step backwards through them.  Parameter gradients (J, D, H,
-// per-site h_i) accumulate in FP64 across sites, stages and steps; partial
-// sums of 32 sites (J, D, H) and of one checkpoint segment (h_i) are formed in
-// the state precision first.
+// per-site h_i) accumulate in FP64: each site's term of each stage is formed
+// in the state precision (like the forward stencil) and added in FP64, into
+// the caller's FP64 field-gradient array (h_i) or into FP64 per-thread sums
+// that are reduced in FP64 (J, D, H).
 //
 // Transposes used (f the right-hand side of Eq. LLL at fixed noise, a = s x H):
 //   w_i = (df_i/dH_i)^T v_i = -(s x v) - lambda s x (s x v)    [slow: without -(s x v)]
@@ -148,14 +149,14 @@ __global__ void k_adj_lincomb(real* __restrict__ out, const real* __restrict__ s
 }
 
 // Stage transpose, site-local part ("w-part") at site i for the stage with
-// input x and v = dt lam_K: w and u, the per-site field gradient gseg += w,
-// and the site's terms of <w, sum_nn x> (J), 2 x_z w_z (D) and w (H) added to
-// the thread's partial sums p[5].
+// input x and v = dt lam_K: w and u, the per-site field gradient gh += w (in
+// FP64), and the site's terms of <w, sum_nn x> (J), 2 x_z w_z (D) and w (H)
+// added in FP64 to the thread's sums p[5].
 template <typename real, bool PREC, bool HSITE>
 __device__ __forceinline__ void w_part(const real* __restrict__ x, const real* __restrict__ hs, long long i,
                                        const long long nb[6], const real wn[6], long long N, real J, real twoD,
                                        const real H[3], real lambda, const real v[3], real* __restrict__ w,
-                                       real* __restrict__ u, real* __restrict__ gseg, real p[5]) {
+                                       real* __restrict__ u, double* __restrict__ gh, double p[5]) {
     const real s[3] = {x[i], x[N + i], x[2 * N + i]};
     real sn[3], hr[3];
 #pragma unroll
@@ -188,24 +189,21 @@ __device__ __forceinline__ void w_part(const real* __restrict__ x, const real* _
         }
         w[c * N + i] = wi[c];
         u[c * N + i] = ui;
-        if (gseg) gseg[c * N + i] += wi[c];
+        if (gh) gh[c * N + i] += (double)wi[c];
     }
-    p[0] += wi[0] * sn[0] + wi[1] * sn[1] + wi[2] * sn[2];
-    p[1] += real(2) * s[2] * wi[2];
-    p[2] += wi[0];
-    p[3] += wi[1];
-    p[4] += wi[2];
+    p[0] += (double)(wi[0] * sn[0] + wi[1] * sn[1] + wi[2] * sn[2]);
+    p[1] += (double)(real(2) * s[2] * wi[2]);
+    p[2] += (double)wi[0];
+    p[3] += (double)wi[1];
+    p[4] += (double)wi[2];
 }
 
-// Block partials of the w-parts: the terms of one warp are summed in the
-// state precision (32 terms); the warp sums are converted once and added in
-// FP64 into the block's record, so the long sums over sites, stages and
-// steps are FP64 while the FP64 pipe (narrow on this GPU) sees a few
-// operations per warp instead of several per site.  Each block adds into its
-// own record, launch after launch in stream order (deterministic); the
-// records are summed once after the backward pass.
-template <typename real>
-__device__ __forceinline__ void flush_partials(real p[5], double* __restrict__ partials) {
+// Block partials of the w-parts: the threads' FP64 sums are reduced in FP64
+// (warp shuffles, then the block's warps in a fixed order) and added into the
+// block's record.  Each block adds into its own record, launch after launch in
+// stream order (deterministic); the records are summed once after the
+// backward pass.
+__device__ __forceinline__ void flush_partials(double p[5], double* __restrict__ partials) {
     __shared__ double red[kAT / 32][5];
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
@@ -214,7 +212,7 @@ __device__ __forceinline__ void flush_partials(real p[5], double* __restrict__ p
     }
     if ((threadIdx.x & 31) == 0)
 #pragma unroll
-        for (int q = 0; q < 5; ++q) red[threadIdx.x >> 5][q] = (double)p[q];
+        for (int q = 0; q < 5; ++q) red[threadIdx.x >> 5][q] = p[q];
     __syncthreads();
     if (threadIdx.x < 5) {
         double t = 0;
@@ -248,14 +246,14 @@ struct TopArgs {
     const real* hs;
     real* w;             // w, u of stage S-1
     real* u;
-    real* gseg;
+    double* gh;          // FP64 field gradient (3N) or null
     double* partials;
 };
 
 template <typename real, bool PREC, bool HSITE, int S>
 __global__ void __launch_bounds__(kAT, kAdjMinBlocks) k_adj_top_w(TopArgs<real> a, AdjGeom<real> G) {
     const long long N = (long long)G.nx * G.ny * G.nz;
-    real p[5] = {0, 0, 0, 0, 0};
+    double p[5] = {0, 0, 0, 0, 0};
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
         real l0 = a.lam[i], l1 = a.lam[N + i], l2 = a.lam[2 * N + i];
         if (a.pulse) {
@@ -288,9 +286,9 @@ __global__ void __launch_bounds__(kAT, kAdjMinBlocks) k_adj_top_w(TopArgs<real> 
         neighbours_w<real>(i, G.nx, G.ny, G.nz, G.bc, nb, wn);
         const real bl = a.b[S - 1] * G.dt;
         const real v[3] = {bl * l0, bl * l1, bl * l2};
-        w_part<real, PREC, HSITE>(a.xlast, a.hs, i, nb, wn, N, G.J, G.twoD, G.H, G.lambda, v, a.w, a.u, a.gseg, p);
+        w_part<real, PREC, HSITE>(a.xlast, a.hs, i, nb, wn, N, G.J, G.twoD, G.H, G.lambda, v, a.w, a.u, a.gh, p);
     }
-    flush_partials<real>(p, a.partials);
+    flush_partials(p, a.partials);
 }
 
 // Stage j of the transposed step: the neighbour part ("x-part") of stage j,
@@ -310,14 +308,14 @@ struct XWArgs {
     const real* hs;
     real* wn;            // w, u of stage j-1
     real* un;
-    real* gseg;
+    double* gh;          // FP64 field gradient (3N) or null
     double* partials;
 };
 
 template <typename real, bool PREC, bool HSITE, int NL, bool W>
 __global__ void __launch_bounds__(kAT, kAdjMinBlocks) k_adj_xw(XWArgs<real> a, AdjGeom<real> G) {
     const long long N = (long long)G.nx * G.ny * G.nz;
-    real p[5] = {0, 0, 0, 0, 0};
+    double p[5] = {0, 0, 0, 0, 0};
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
         long long nb[6];
         real wn[6];
@@ -344,21 +342,10 @@ __global__ void __launch_bounds__(kAT, kAdjMinBlocks) k_adj_xw(XWArgs<real> a, A
         if (W) {
             const real v[3] = {G.dt * lk[0], G.dt * lk[1], G.dt * lk[2]};
             w_part<real, PREC, HSITE>(a.xprev, a.hs, i, nb, wn, N, G.J, G.twoD, G.H, G.lambda, v, a.wn, a.un,
-                                      a.gseg, p);
+                                      a.gh, p);
         }
     }
-    if (W) flush_partials<real>(p, a.partials);
-}
-
-// gh += gseg (FP64), gseg = 0: the field gradient of one checkpoint segment,
-// summed over its stages in the state precision, folded into the run's FP64
-// total.
-template <typename real>
-__global__ void k_adj_fold(double* __restrict__ gh, real* __restrict__ gseg, long long len) {
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < len; q += (long long)gridDim.x * blockDim.x) {
-        gh[q] += (double)gseg[q];
-        gseg[q] = real(0);
-    }
+    if (W) flush_partials(p, a.partials);
 }
 
 // acc[q] += sum over blocks of partials[b*5+q], fixed order (deterministic).
@@ -465,7 +452,7 @@ size_t adjoint_workspace_bytes(const Geom& g, int elt, const Tableau& tb, int pa
         b += al(comp) * (size_t)(2 * stages - 1) * (size_t)K;   // X_j (j >= 2) and K_j of every step of a segment
     b += al(comp) * (size_t)(K + 1);     // segment states
     b += al(comp) * (size_t)stages * 3;  // X_j, K_j, lam_K_j
-    b += al(comp) * 7;                   // y, lam, w and u (two pairs), segment field gradient
+    b += al(comp) * 6;                   // y, lam, w and u (two pairs)
     b += al(sizeof(double) * 5 * (size_t)adjoint_blocks(g));
     b += al(sizeof(double) * 8);         // accumulators
     b += al(sizeof(long long));          // pulse-number slot
@@ -568,8 +555,6 @@ cudaError_t adjoint_run(const AdjointRun<real>& A) {
         ub[q] = reinterpret_cast<real*>(ws + off);
         off += al(compb);
     }
-    real* gseg = A.g_h ? reinterpret_cast<real*>(ws + off) : nullptr;  // field gradient of one segment
-    off += al(compb);
     const int nb = adjoint_blocks(g);
     double* partials = reinterpret_cast<double*>(ws + off);
     off += al(sizeof(double) * 5 * (size_t)nb);
@@ -618,11 +603,9 @@ cudaError_t adjoint_run(const AdjointRun<real>& A) {
                                                     H2, A.dLdE, A.dLdM[0], A.dLdM[1], A.dLdM[2], A.bc);
     k_adj_seed_finish<<<1, kAT, 0, st>>>(partials, nb, acc, A.dLdE, (double)N);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    // per-block FP64 records of the stage transposes and the segment field
-    // gradient start at zero
+    // per-block FP64 records of the stage transposes start at zero
     e = cudaMemsetAsync(partials, 0, sizeof(double) * 5 * (size_t)nb, st);
     if (e != cudaSuccess) return e;
-    if (gseg && (e = cudaMemsetAsync(gseg, 0, compb, st)) != cudaSuccess) return e;
 
     const long long total = A.n_end - A.n0;
     const int nseg = (int)((total + A.K - 1) / A.K);
@@ -713,7 +696,7 @@ cudaError_t adjoint_run(const AdjointRun<real>& A) {
             ta.hs = hs;
             ta.w = wb[(S - 1) & 1];
             ta.u = ub[(S - 1) & 1];
-            ta.gseg = gseg;
+            ta.gh = A.g_h;
             ta.partials = partials;
             launch_top_w<real>(A.precession != 0, HS, S, ta, G, nb, st);
             for (int j = S - 1; j >= 0; --j) {
@@ -731,13 +714,12 @@ cudaError_t adjoint_run(const AdjointRun<real>& A) {
                     xa.un = ub[(j - 1) & 1];
                 }
                 xa.hs = hs;
-                xa.gseg = gseg;
+                xa.gh = A.g_h;
                 xa.partials = partials;
                 launch_xw<real>(A.precession != 0, HS, j, xa, G, nb, st);
             }
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
-        if (gseg) k_adj_fold<real><<<grid_for(len), kAT, 0, st>>>(A.g_h, gseg, len);
     }
     k_adj_accumulate<<<1, kAT, 0, st>>>(partials, nb, acc, 1.0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -314,20 +314,28 @@ constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mutex;
 double* g_noalloc_addr[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device, looked up once
-// per device.  In host code the array's name is only a host-side stand-in,
-// so its address must come from cudaGetSymbolAddress.
-cudaError_t noalloc_scratch(double** out) {
+// Device address of the scratch array on the current device.  In host code
+// the array's name is only a host-side stand-in, so its address must come
+// from cudaGetSymbolAddress, called with the device current.  Outside stream
+// capture it is looked up on every call (a cudaDeviceReset reloads the module
+// and may move the array); a call on a capturing stream reuses the address
+// the last uncaptured call found on this device.
+cudaError_t noalloc_scratch(cudaStream_t st, double** out) {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(st, &cap);
+    if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_addr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_partials);
         if (e != cudaSuccess) return e;
         g_noalloc_addr[dev] = static_cast<double*>(p);
+    } else if (!g_noalloc_addr[dev]) {
+        return cudaErrorStreamCaptureUnsupported;
     }
     *out = g_noalloc_addr[dev];
     return cudaSuccess;
@@ -338,24 +346,27 @@ cudaError_t noalloc_scratch(double** out) {
 
 extern "C" int spin_observables_noalloc(int32_t precision, const void* sx, const void* sy, const void* sz,
                                         const void* h_site, int32_t nx, int32_t ny, int32_t nz, double J, double D,
-                                        const double H[3], double* out5, void* cuda_stream) {
+                                        const double H[3], int32_t bc, double* out5, void* cuda_stream) {
     using namespace spin;
     if (!sx || !sy || !sz || !out5 || !H) return SPIN_EINVAL;
+    if (bc != 0 && bc != 1) return SPIN_EINVAL;
     if (precision != 32 && precision != 64) return SPIN_EINVAL;
     if (nx < 1 || ny < 1 || nz < 1) return SPIN_EINVAL;
     const Geom g{nx, ny, nz};
     if (g.N() > (long long)SPIN_NOALLOC_MAX_SITES) return SPIN_EINVAL;  // beyond the stated maximum
     const int nblocks = observables_blocks(g);
     if (nblocks > kNoAllocMaxBlocks) return SPIN_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     double* scratch = nullptr;
-    if (noalloc_scratch(&scratch) != cudaSuccess) return SPIN_ECUDA;
+    const cudaError_t es = noalloc_scratch(st, &scratch);
+    if (es == cudaErrorStreamCaptureUnsupported) return SPIN_EINVAL;
+    if (es != cudaSuccess) return SPIN_ECUDA;
     Phys<double> ph{};
     ph.J = J;
     ph.twoD = 2.0 * D;
     ph.H[0] = H[0];
     ph.H[1] = H[1];
     ph.H[2] = H[2];
-    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     const size_t comp = (size_t)(precision == 64 ? 8 : 4) * (size_t)g.N();
     cudaError_t e;
     if (precision == 32) {
@@ -363,13 +374,13 @@ extern "C" int spin_observables_noalloc(int32_t precision, const void* sx, const
         const float* hs[3] = {nullptr, nullptr, nullptr};
         if (h_site)
             for (int c = 0; c < 3; ++c) hs[c] = (const float*)((const char*)h_site + c * comp);
-        e = launch_observables<float>(s, hs, g, ph, scratch, nblocks, out5, nullptr, 0, nullptr, nullptr, 1, st);
+        e = launch_observables<float>(s, hs, g, ph, scratch, nblocks, out5, nullptr, 0, nullptr, nullptr, 1, st, bc);
     } else {
         const double* s[3] = {(const double*)sx, (const double*)sy, (const double*)sz};
         const double* hs[3] = {nullptr, nullptr, nullptr};
         if (h_site)
             for (int c = 0; c < 3; ++c) hs[c] = (const double*)((const char*)h_site + c * comp);
-        e = launch_observables<double>(s, hs, g, ph, scratch, nblocks, out5, nullptr, 0, nullptr, nullptr, 1, st);
+        e = launch_observables<double>(s, hs, g, ph, scratch, nblocks, out5, nullptr, 0, nullptr, nullptr, 1, st, bc);
     }
     return e == cudaSuccess ? SPIN_OK : SPIN_ECUDA;
 }

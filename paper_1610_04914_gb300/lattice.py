@@ -127,16 +127,31 @@ def spin_noise_draw(seed: int, k: int, replica: int, n_sites: int, precision: in
 
 
 def spin_observables_noalloc(state: torch.Tensor, J: float, D: float, H, out5: torch.Tensor,
-                             h_site: torch.Tensor | None = None, stream=None) -> None:
+                             h_site: torch.Tensor | None = None, bc: int = 0, stream=None) -> None:
     """M and E of a (3, nz, ny, nx) state into the device tensor out5 (5 doubles:
     M_x, M_y, M_z, E, non-finite count) without any allocation; asynchronous.
-    For callers that cannot allocate device memory at the call site."""
+    For callers that cannot allocate device memory at the call site.  bc: 0
+    periodic, 1 free boundaries.  The arguments are checked here before any
+    pointer reaches the library (a wrong dtype, shape or device would make the
+    kernel read or write outside the tensors)."""
+    if not (isinstance(state, torch.Tensor) and state.is_cuda and state.dim() == 4 and state.shape[0] == 3
+            and state.is_contiguous() and state.dtype in (torch.float32, torch.float64)):
+        raise ValueError("state must be a contiguous CUDA float32/float64 tensor of shape (3, nz, ny, nx)")
+    if not (isinstance(out5, torch.Tensor) and out5.is_cuda and out5.dtype == torch.float64
+            and out5.is_contiguous() and out5.numel() >= 5 and out5.device == state.device):
+        raise ValueError("out5 must be a contiguous CUDA float64 tensor of at least 5 elements on the state's device")
+    if h_site is not None and not (isinstance(h_site, torch.Tensor) and h_site.dtype == state.dtype
+                                   and h_site.device == state.device and h_site.is_contiguous()
+                                   and h_site.numel() == state.numel()):
+        raise ValueError("h_site must be a contiguous tensor of the state's dtype, device and size (3N)")
+    if int(bc) not in (0, 1):
+        raise ValueError("bc must be 0 (periodic) or 1 (free)")
     _, nz, ny, nx = state.shape
     prec = 64 if state.dtype == torch.float64 else 32
-    Hc = (ctypes.c_double * 3)(*H)
+    Hc = (ctypes.c_double * 3)(*[float(v) for v in H])
     check(B.load().spin_observables_noalloc(prec, state[0].data_ptr(), state[1].data_ptr(), state[2].data_ptr(),
                                             h_site.data_ptr() if h_site is not None else None, nx, ny, nz,
-                                            float(J), float(D), Hc, out5.data_ptr(), _stream_ptr(stream)))
+                                            float(J), float(D), Hc, int(bc), out5.data_ptr(), _stream_ptr(stream)))
 
 
 def spin_record_store_size(p: Params, K: int, nsteps: int) -> int:
@@ -239,13 +254,15 @@ class Lattice:
 
 class SpinRunFn(torch.autograd.Function):
     """(E, M) of the final state after nsteps pulse-noise steps from s0, with
-    pathwise gradients (noise fixed) w.r.t. J, D and the per-site field h
-    through the library's checkpointed adjoint (checkpoint every K steps)."""
+    pathwise gradients (noise fixed) w.r.t. J, D, the uniform field H (3) and
+    the per-site field h through the library's checkpointed adjoint
+    (checkpoint every K steps).  dL/dH = sum_i dL/dh_i, accumulated in FP64."""
 
     @staticmethod
-    def forward(ctx, J, D, h_site, s0, p: Params, nsteps: int, K: int):
+    def forward(ctx, J, D, H, h_site, s0, p: Params, nsteps: int, K: int):
         import dataclasses
-        q = dataclasses.replace(p, J=float(J), D=float(D))
+        Hv = tuple(float(v) for v in torch.as_tensor(H, dtype=torch.float64).reshape(3).tolist())
+        q = dataclasses.replace(p, J=float(J), D=float(D), H=Hv)
         lat = Lattice(q, s0.detach(), h_site=h_site.detach(), device=s0.device)
         lat.record(K, nsteps)
         lat.step(nsteps)
@@ -253,6 +270,7 @@ class SpinRunFn(torch.autograd.Function):
         ctx.lat = lat
         ctx.h_shape = h_site.shape
         ctx.h_dtype = h_site.dtype
+        ctx.H_meta = (torch.as_tensor(H).dtype, torch.as_tensor(H).device, torch.as_tensor(H).shape)
         return (torch.tensor(E, dtype=torch.float64, device=s0.device),
                 torch.tensor(M, dtype=torch.float64, device=s0.device))
 
@@ -261,10 +279,12 @@ class SpinRunFn(torch.autograd.Function):
         g = ctx.lat.backward(gM.detach().cpu().tolist(), float(gE.detach().cpu()), field_grad=True)
         ctx.lat.close()
         dev = gE.device
+        h_dtype, h_dev, h_shape = ctx.H_meta
+        gH = torch.tensor(g["H"], dtype=torch.float64).to(device=h_dev, dtype=h_dtype).reshape(h_shape)
         return (torch.tensor(g["J"], dtype=torch.float64, device=dev),
                 torch.tensor(g["D"], dtype=torch.float64, device=dev),
+                gH,
                 g["h"].reshape(ctx.h_shape).to(ctx.h_dtype), None, None, None, None)
-
 
 
 def _host_doubles(vals):

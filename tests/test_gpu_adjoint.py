@@ -75,19 +75,22 @@ def test_adjoint_full_size_64cubed(gpu, orc):
 
 def test_autograd_function(gpu):
     """SpinRunFn wraps the forward run and spin_backward as a
-    torch.autograd.Function: its gradients equal the direct call."""
+    torch.autograd.Function: its gradients w.r.t. J, D, H and h equal the
+    direct call's, and dL/dH is the sum of dL/dh_i."""
     shape = (8, 8, 8)
     p = gpu.Params(*shape, J=1.0, D=0.05, H=(0, 0, 0), lam=0.05, T=0.8, dt=0.1, R=10, seed=5, precision=32)
     s0 = torch.from_numpy(spin_inputs.random_spins(*shape, seed=5)).float().cuda()
     hs = torch.from_numpy(spin_inputs.site_fields(*shape, 0.01, seed=5)).float().cuda()
     J = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
     D = torch.tensor(0.05, dtype=torch.float64, requires_grad=True)
+    H = torch.tensor([0.01, -0.02, 0.03], dtype=torch.float64, requires_grad=True)
     h = hs.clone().requires_grad_(True)
-    E, M = gpu.SpinRunFn.apply(J, D, h, s0, p, 30, 10)
+    E, M = gpu.SpinRunFn.apply(J, D, H, h, s0, p, 30, 10)
     m_target = torch.tensor([0.0, 0.0, 0.5], dtype=torch.float64, device=M.device)
     loss = E + ((M - m_target) ** 2).sum()
     loss.backward()
-    lat = gpu.Lattice(p, s0, h_site=hs)
+    import dataclasses
+    lat = gpu.Lattice(dataclasses.replace(p, H=(0.01, -0.02, 0.03)), s0, h_site=hs)
     lat.record(10, 30)
     lat.step(30)
     Md, Ed = lat.observables()
@@ -96,4 +99,9 @@ def test_autograd_function(gpu):
     g = lat.backward(dLdM, 1.0)
     assert abs(J.grad.item() - g["J"]) <= 1e-12 * max(1.0, abs(g["J"]))
     assert abs(D.grad.item() - g["D"]) <= 1e-12 * max(1.0, abs(g["D"]))
+    for a in range(3):
+        assert abs(H.grad[a].item() - g["H"][a]) <= 1e-12 * max(1.0, abs(g["H"][a]))
     assert torch.allclose(h.grad.double(), g["h"].float().double(), rtol=1e-6, atol=1e-9)
+    # dL/dH = sum_i dL/dh_i (the uniform field enters H_eff like every h_i)
+    hsum = g["h"].reshape(3, -1).sum(dim=1).cpu().numpy()
+    assert np.max(np.abs(hsum - np.array(g["H"]))) <= 1e-9 * max(1.0, float(np.max(np.abs(hsum))))

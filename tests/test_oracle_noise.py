@@ -172,3 +172,19 @@ def test_pulses_only_at_scheduled_steps(orc):
         if changed:
             assert np.allclose(cur, orc.pulse(p, prev, orc.pulse_number(n, 6)), atol=1e-15)
         prev = cur
+
+
+def test_openmp_build_is_bitwise_serial(orc):
+    """The OpenMP build of the oracle (whole-lattice loops over z-planes on all
+    host cores, used for the all-cores CPU baseline) computes every site with
+    the same expression as the serial build: bitwise equal states and samples
+    over 25 steps with two pulses, and for the slow equation and RK5."""
+    import spin_inputs
+    if orc.build_omp() is None:
+        pytest.skip("gcc without OpenMP")
+    for kw in (dict(), dict(precession=0, integrator=orc.RK2_MIDPOINT), dict(integrator=orc.RK5_BUTCHER, bc=1)):
+        p = orc.Params(16, 12, 10, J=1.0, D=0.05, H=(0, 0, 0.1), lam=0.1, T=1.0, dt=0.1, R=10, seed=1, **kw)
+        s0 = spin_inputs.random_spins(16, 12, 10, seed=0)
+        a, sa = orc.run(p, s0, 25)
+        b, sb = orc.run(p, s0, 25, threads=True)
+        assert np.array_equal(a, b) and np.array_equal(sa, sb)
