@@ -3,8 +3,15 @@ oracle's own discrete adjoint on identical inputs and noise.
 
 Tolerances.  FP64 state: the GPU recomputes the same steps, so gradients agree
 to rounding (relative 1e-9 of each gradient's largest entry).  FP32 state and
-adjoint: 20 steps of float rounding in the forward states and the transposed
-stages; relative 1e-3 of the largest entry (measured ~1e-5)."""
+adjoint against the FP64 oracle: every forward stage and every transposed
+stage rounds its result to float (relative 2^-24 = 6e-8), so over 20 steps of
+4 stages the gradients carry at most ~80 such roundings, accumulated
+linearly: ~5e-6 of the largest entry.  The bound used is 1e-5 (the measured
+errors over these cases are 1e-8..5.4e-7 for J, D, H and 6e-7..1.9e-6 for
+dL/dh_i and dL/ds_0).  dL/dh_i and dL/ds_0 are also checked element by element:
+|g_i - r_i| <= 2e-4 |r_i| + 1e-5 max|r| (measured: at most 6e-5 |r_i| +
+6e-7 max|r|), so a dropped term that is small against the largest entry but
+not against its own element fails."""
 import numpy as np
 import pytest
 import torch
@@ -18,6 +25,15 @@ pytestmark = pytest.mark.gpu
 def _rel(a, b):
     a, b = np.asarray(a, dtype=float), np.asarray(b, dtype=float)
     return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+TOL32 = 1e-5
+
+
+def _elementwise_ok(a, b, rtol=2e-4, atol_rel=1e-5):
+    """|a_i - b_i| <= rtol |b_i| + atol_rel max|b| for every element."""
+    a, b = np.asarray(a, dtype=float).ravel(), np.asarray(b, dtype=float).ravel()
+    return bool(np.all(np.abs(a - b) <= rtol * np.abs(b) + atol_rel * np.max(np.abs(b))))
 
 
 CASES = [  # precision, integrator, precession, K
@@ -40,12 +56,15 @@ def test_adjoint_matches_oracle(gpu, orc, prec, integ, precession, K):
     dLdM, dLdE = [0.3, -0.2, 0.7], 1.0
     g = lat.backward(dLdM, dLdE, field_grad=True, state_grad=True)
     ref = orc.adjoint(orc_params(orc, p), as_input(p, s0), nsteps, dLdM, dLdE, h_site=as_input(p, hs))
-    tol = 1e-9 if prec == 64 else 1e-3
+    tol = 1e-9 if prec == 64 else TOL32
     assert _rel(g["J"], ref["J"]) < tol
     assert _rel(g["D"], ref["D"]) < tol
     assert _rel(g["H"], ref["H"]) < tol
     assert _rel(g["h"].cpu().numpy(), ref["h"]) < tol
     assert _rel(g["s0"].double().cpu().numpy(), ref["s0"]) < tol
+    if prec == 32:
+        assert _elementwise_ok(g["h"].cpu().numpy(), ref["h"])
+        assert _elementwise_ok(g["s0"].double().cpu().numpy(), ref["s0"])
 
 
 def test_adjoint_full_size_64cubed(gpu, orc):
@@ -67,10 +86,11 @@ def test_adjoint_full_size_64cubed(gpu, orc):
     dLdM = [2.0 * (M[a] - w["m_target"][a]) for a in range(3)]
     g = lat.backward(dLdM, 1.0, field_grad=True)
     ref = orc.adjoint(orc_params(orc, p), as_input(p, s0), nsteps, dLdM, 1.0, h_site=as_input(p, hs))
-    assert _rel(g["J"], ref["J"]) < 1e-3
-    assert _rel(g["D"], ref["D"]) < 1e-3
-    assert _rel(g["H"], ref["H"]) < 1e-3
-    assert _rel(g["h"].cpu().numpy(), ref["h"]) < 1e-3
+    assert _rel(g["J"], ref["J"]) < TOL32
+    assert _rel(g["D"], ref["D"]) < TOL32
+    assert _rel(g["H"], ref["H"]) < TOL32
+    assert _rel(g["h"].cpu().numpy(), ref["h"]) < TOL32
+    assert _elementwise_ok(g["h"].cpu().numpy(), ref["h"])
 
 
 def test_autograd_function(gpu):

@@ -59,9 +59,14 @@ def test_adjoint_free(gpu, orc, prec):
     lat.step(20)
     g = lat.backward([0.3, -0.2, 0.7], 1.0, field_grad=True)
     ref = orc.adjoint(orc_params(orc, p), as_input(p, s0), 20, [0.3, -0.2, 0.7], 1.0, h_site=as_input(p, hs))
-    tol = 1e-9 if prec == 64 else 1e-3
+    # same bounds as the periodic adjoint tests (test_gpu_adjoint.py): FP32
+    # 1e-5 of the largest entry and 2e-4 |r_i| + 1e-5 max|r| per element
+    tol = 1e-9 if prec == 64 else 1e-5
     for key in ("J", "D", "H"):
         a, b = np.asarray(g[key], float), np.asarray(ref[key], float)
         assert np.max(np.abs(a - b)) / np.max(np.abs(b)) < tol, key
     hg = g["h"].cpu().numpy()
     assert np.max(np.abs(hg - ref["h"])) / np.max(np.abs(ref["h"])) < tol
+    if prec == 32:
+        r = ref["h"]
+        assert np.all(np.abs(hg - r) <= 2e-4 * np.abs(r) + 1e-5 * np.max(np.abs(r)))
