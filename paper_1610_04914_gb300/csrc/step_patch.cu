@@ -251,8 +251,13 @@ __device__ __forceinline__ void patch_iteration(const PatchArgs& a, PRings<S, HS
 #pragma unroll
     for (int j = 1; j <= S; ++j) {
         // the 2*PY rows of warp w take part in stage j only if they meet the
-        // rows [j, ROWS-j) where stage j is still needed (warp-uniform)
-        const bool active = (2 * PY * th.warp_row + 2 * PY - 1 >= j) && (2 * PY * th.warp_row < ROWS - j);
+        // rows [j, ROWS-j) where stage j is still needed, and only once the
+        // march has reached the planes stage j is needed on: stage j serves
+        // planes z0-(S-j) .. z0+tz+(S-j)-1, which it reaches at iteration
+        // i = 2j-2 (earlier iterations would compute planes no later stage
+        // reads; the test is warp-uniform)
+        const bool active = (2 * PY * th.warp_row + 2 * PY - 1 >= j) && (2 * PY * th.warp_row < ROWS - j) &&
+                            (i >= 2 * j - 2);
         const int slot = (P + S - j) & 3;
         const int sm = (slot + 3) & 3, sp = (slot + 1) & 3;
         if (active) {
