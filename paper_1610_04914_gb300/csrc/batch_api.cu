@@ -45,6 +45,7 @@ struct spin_batch {
     double* partials;
     double* out;
     long long* d_interval;
+    int* d_status;           // bit 0: a bounded device wait gave up
     long long* d_sample_count;
     double* ring;
     long long samples_read;
@@ -140,7 +141,7 @@ int obs_blocks(int nrep, const int32_t* L, std::vector<ObsBlock>* blocks, std::v
 }
 
 struct BLayout {
-    size_t alt[3], reps, items, oblocks, first, partials, out, interval, count, ring, total;
+    size_t alt[3], reps, items, oblocks, first, partials, out, interval, count, status, ring, total;
 };
 
 BLayout blayout(const spin_params* p, int nrep, const int32_t* L) {
@@ -171,6 +172,8 @@ BLayout blayout(const spin_params* p, int nrep, const int32_t* L) {
     off += al(sizeof(long long));
     b.count = off;
     off += al(sizeof(long long));
+    b.status = off;
+    off += al(sizeof(int));
     b.ring = off;
     off += al(sizeof(double) * 5 * (size_t)nrep * SPIN_BATCH_SAMPLE_RING);
     b.total = off;
@@ -196,6 +199,7 @@ StepLaunch<float> batch_launch_args(spin_batch* b, int from, bool pulse, cudaStr
     Ls.pulse = pulse ? 1 : 0;
     Ls.seed = b->p.seed;
     Ls.d_interval = b->d_interval;
+    Ls.d_status = b->d_status;
     Ls.stream = st;
     return Ls;
 }
@@ -389,6 +393,7 @@ int spin_batch_create(const spin_params* p, int32_t nrep, const int32_t* L, cons
     b->out = reinterpret_cast<double*>(ws + Lo.out);
     b->d_interval = reinterpret_cast<long long*>(ws + Lo.interval);
     b->d_sample_count = reinterpret_cast<long long*>(ws + Lo.count);
+    b->d_status = reinterpret_cast<int*>(ws + Lo.status);
     b->ring = reinterpret_cast<double*>(ws + Lo.ring);
     int rc = SPIN_OK;
     do {
@@ -402,7 +407,8 @@ int spin_batch_create(const spin_params* p, int32_t nrep, const int32_t* L, cons
         if (cudaMemcpy(b->oblocks, ob.data(), sizeof(ObsBlock) * ob.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaMemcpy(b->first_block, fb.data(), sizeof(int) * fb.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaMemsetAsync(b->d_interval, 0, sizeof(long long), b->st) != cudaSuccess ||
-            cudaMemsetAsync(b->d_sample_count, 0, sizeof(long long), b->st) != cudaSuccess) {
+            cudaMemsetAsync(b->d_sample_count, 0, sizeof(long long), b->st) != cudaSuccess ||
+            cudaMemsetAsync(b->d_status, 0, sizeof(int), b->st) != cudaSuccess) {
             rc = SPIN_ECUDA;
             break;
         }
@@ -465,8 +471,11 @@ int spin_batch_step_pulse(spin_batch* b, int64_t nsteps) {
 int spin_batch_observables(spin_batch* b, double* out) {
     if (!b || !out) return SPIN_EINVAL;
     BATCH_CUDA(b, batch_observe(b, b->cur, false, b->st));
+    int status = 0;
     BATCH_CUDA(b, cudaMemcpyAsync(out, b->out, sizeof(double) * 5 * (size_t)b->nrep, cudaMemcpyDeviceToHost, b->st));
+    BATCH_CUDA(b, cudaMemcpyAsync(&status, b->d_status, sizeof(int), cudaMemcpyDeviceToHost, b->st));
     BATCH_CUDA(b, cudaStreamSynchronize(b->st));
+    if (status & 1) return bset_err(b, SPIN_ETIMEOUT, "a bounded wait in the fused step gave up; the state is invalid");
     for (int r = 0; r < b->nrep; ++r)
         if (out[5 * r + 4] != 0.0) return bset_err(b, SPIN_ENONFINITE, "replica %d has non-finite spins", r);
     return SPIN_OK;
@@ -475,8 +484,11 @@ int spin_batch_observables(spin_batch* b, double* out) {
 int spin_batch_samples(spin_batch* b, double* out, int64_t max_records, int64_t* count) {
     if (!b || !count || max_records < 0 || (max_records > 0 && !out)) return SPIN_EINVAL;
     long long total = 0;
+    int status = 0;
     BATCH_CUDA(b, cudaMemcpyAsync(&total, b->d_sample_count, sizeof(total), cudaMemcpyDeviceToHost, b->st));
+    BATCH_CUDA(b, cudaMemcpyAsync(&status, b->d_status, sizeof(int), cudaMemcpyDeviceToHost, b->st));
     BATCH_CUDA(b, cudaStreamSynchronize(b->st));
+    if (status & 1) return bset_err(b, SPIN_ETIMEOUT, "a bounded wait in the fused step gave up; the state is invalid");
     long long first = b->samples_read;
     if (total - first > SPIN_BATCH_SAMPLE_RING) first = total - SPIN_BATCH_SAMPLE_RING;
     if (total - first > max_records) first = total - max_records;

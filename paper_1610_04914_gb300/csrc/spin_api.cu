@@ -33,6 +33,7 @@ struct spin_lattice {
     double* out_obs;
     long long* d_interval;
     long long* d_sample_count;
+    int* d_status;           // bit 0: a bounded device wait gave up
     double* ring;
     long long samples_read;
     cudaGraphExec_t graph[2];  // one noise interval starting from buffer 0 / 1
@@ -54,7 +55,7 @@ struct Layout {
     size_t alt[3];
     size_t tmp;
     size_t partials;
-    size_t out_sample, out_obs, interval, sample_count, ring;
+    size_t out_sample, out_obs, interval, sample_count, status, ring;
     size_t total;
 };
 
@@ -102,6 +103,8 @@ Layout layout_for(const spin_params* p) {
     off += align_up(sizeof(long long));
     L.sample_count = off;
     off += align_up(sizeof(long long));
+    L.status = off;
+    off += align_up(sizeof(int));
     L.ring = off;
     off += align_up(sizeof(double) * 5 * SPIN_SAMPLE_RING);
     L.total = off;
@@ -148,6 +151,7 @@ StepLaunch<real> make_launch(spin_lattice* h, int from, bool pulse) {
     L.replica = (uint64_t)h->p.replica;
     L.sigma = (real)std::sqrt(2.0 * h->p.lambda * h->p.T * h->p.steps_per_pulse * std::fabs(h->p.dt));
     L.d_interval = h->d_interval;
+    L.d_status = h->d_status;
     L.tmp = static_cast<real*>(h->tmp);
     L.stream = h->st;
     L.force_generic = h->p.path == 1;
@@ -283,6 +287,9 @@ int backward_t(spin_lattice* h, const double dLdM[3], double dLdE, void* ws, dou
     A.g_s0 = static_cast<real*>(g_s0);
     if (g_h_site) SPIN_CUDA(h, cudaMemsetAsync(g_h_site, 0, sizeof(double) * 3 * (size_t)h->g.N(), h->st));
     SPIN_CUDA(h, adjoint_run<real>(A));
+    int status = 0;   // the recomputing steps' bounded waits (adjoint_run has synchronised)
+    SPIN_CUDA(h, cudaMemcpy(&status, h->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (status & 1) return set_err(h, SPIN_ETIMEOUT, "a bounded wait in the fused step gave up; the gradients are invalid");
     return SPIN_OK;
 }
 
@@ -348,12 +355,14 @@ int spin_lattice_create(const spin_params* p, void* sx, void* sy, void* sz, cons
     h->out_obs = reinterpret_cast<double*>(ws + L.out_obs);
     h->d_interval = reinterpret_cast<long long*>(ws + L.interval);
     h->d_sample_count = reinterpret_cast<long long*>(ws + L.sample_count);
+    h->d_status = reinterpret_cast<int*>(ws + L.status);
     h->ring = reinterpret_cast<double*>(ws + L.ring);
     h->err[0] = 0;
 
     cudaError_t e = h->elt == 4 ? prepare_step_kernels<float>() : prepare_step_kernels<double>();
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_interval, 0, sizeof(long long), h->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_sample_count, 0, sizeof(long long), h->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_status, 0, sizeof(int), h->st);
     if (e != cudaSuccess) {
         delete h;
         return SPIN_ECUDA;
@@ -421,8 +430,11 @@ int spin_observables(spin_lattice* h, double M[3], double* E) {
     if (!h || !M || !E) return SPIN_EINVAL;
     SPIN_CUDA(h, observe(h, h->cur, false, h->st));
     double o[5];
+    int status = 0;
     SPIN_CUDA(h, cudaMemcpyAsync(o, h->out_obs, sizeof(o), cudaMemcpyDeviceToHost, h->st));
+    SPIN_CUDA(h, cudaMemcpyAsync(&status, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->st));
     SPIN_CUDA(h, cudaStreamSynchronize(h->st));
+    if (status & 1) return set_err(h, SPIN_ETIMEOUT, "a bounded wait in the fused step gave up; the state is invalid");
     M[0] = o[0];
     M[1] = o[1];
     M[2] = o[2];
@@ -434,8 +446,11 @@ int spin_observables(spin_lattice* h, double M[3], double* E) {
 int spin_samples(spin_lattice* h, double* out, int64_t max_records, int64_t* count) {
     if (!h || !count || (max_records > 0 && !out) || max_records < 0) return SPIN_EINVAL;
     long long total = 0;
+    int status = 0;
     SPIN_CUDA(h, cudaMemcpyAsync(&total, h->d_sample_count, sizeof(total), cudaMemcpyDeviceToHost, h->st));
+    SPIN_CUDA(h, cudaMemcpyAsync(&status, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->st));
     SPIN_CUDA(h, cudaStreamSynchronize(h->st));
+    if (status & 1) return set_err(h, SPIN_ETIMEOUT, "a bounded wait in the fused step gave up; the state is invalid");
     long long first = h->samples_read;
     if (total - first > SPIN_SAMPLE_RING) first = total - SPIN_SAMPLE_RING;
     if (total - first > max_records) first = total - max_records;

@@ -46,6 +46,7 @@ struct StepLaunch {
     uint64_t replica;
     real sigma;            // pulse angle scale sqrt(2 lambda T Delta t)
     const long long* d_interval;  // device: pulse number of the current interval
+    int* d_status;         // device status word (bit 0: a bounded wait in a kernel gave up) or null
     real* tmp;             // generic path: (stages + 1) * 3N scratch
     cudaStream_t stream;
     int force_generic;

@@ -76,6 +76,7 @@ struct PatchArgs {
     float* stx[3][3];
     float* stk[4][3];
     float dt;
+    int* err;          // device status word for bounded waits (nullable; no wait in this kernel sets it)
 };
 
 // A column pair (2m, 2m+1) is contiguous in a row of even length and never
@@ -152,11 +153,11 @@ template <int S>
 __device__ __forceinline__ void issue_plane(const PatchArgs& a, float* stg, const PThread<PatchShape<S>::PY>& th,
                                             int slot, int gz, int tid) {
     constexpr int PY = PatchShape<S>::PY;
-    const long long base = (long long)gz * th.plane;
+    const int base = gz * th.plane;   // site offsets fit in 32 bits (N < 2^31)
     if (a.pair8) {
 #pragma unroll
         for (int rr = 0; rr < PY; ++rr) {
-            const long long o = base + th.col[rr][0];
+            const int o = base + th.col[rr][0];
             cp_async8(stage_pair<S>(stg, slot, 0, rr, tid), a.in0 + o);
             cp_async8(stage_pair<S>(stg, slot, 1, rr, tid), a.in1 + o);
             cp_async8(stage_pair<S>(stg, slot, 2, rr, tid), a.in2 + o);
@@ -166,7 +167,7 @@ __device__ __forceinline__ void issue_plane(const PatchArgs& a, float* stg, cons
         for (int rr = 0; rr < PY; ++rr)
 #pragma unroll
             for (int e = 0; e < 2; ++e) {
-                const long long o = base + th.col[rr][e];
+                const int o = base + th.col[rr][e];
                 cp_async4(stage_pair<S>(stg, slot, 0, rr, tid) + e, a.in0 + o);
                 cp_async4(stage_pair<S>(stg, slot, 1, rr, tid) + e, a.in1 + o);
                 cp_async4(stage_pair<S>(stg, slot, 2, rr, tid) + e, a.in2 + o);
@@ -223,12 +224,12 @@ __device__ __forceinline__ void patch_iteration(const PatchArgs& a, PRings<S, HS
             }
         }
         if (HSITE) {
-            const long long bh = (long long)th.gz_field * th.plane;
+            const int bh = th.gz_field * th.plane;
             th.gz_field = th.gz_field + 1 == a.nz ? 0 : th.gz_field + 1;
             const int sl = (P + S - 1) & 3;
 #pragma unroll
             for (int rr = 0; rr < PY; ++rr) {
-                const long long o0 = bh + th.col[rr][0], o1 = bh + th.col[rr][1];
+                const int o0 = bh + th.col[rr][0], o1 = bh + th.col[rr][1];
                 r.h[sl][rr][0] = make_float2(__ldg(a.hs0 + o0), __ldg(a.hs0 + o1));
                 r.h[sl][rr][1] = make_float2(__ldg(a.hs1 + o0), __ldg(a.hs1 + o1));
                 r.h[sl][rr][2] = make_float2(__ldg(a.hs2 + o0), __ldg(a.hs2 + o1));
@@ -328,11 +329,11 @@ __device__ __forceinline__ void patch_iteration(const PatchArgs& a, PRings<S, HS
                     // stage input and increment of plane t+S-j at the output sites
                     const int pz = t + S - j;
                     if (pz >= z0 && pz < z0 + a.tz && pz < a.nz) {
-                        const long long base = (long long)pz * th.plane;
+                        const int base = pz * th.plane;
 #pragma unroll
                         for (int e = 0; e < 2; ++e) {
                             if (!th.out[rr][e]) continue;
-                            const long long site = base + th.col[rr][e];
+                            const int site = base + th.col[rr][e];
 #pragma unroll
                             for (int c = 0; c < 3; ++c) {
                                 const f2 kk = mul2(sp2(a.dt), f[c]);
@@ -354,7 +355,7 @@ __device__ __forceinline__ void patch_iteration(const PatchArgs& a, PRings<S, HS
         }
         if (j == S && active && t >= z0 && t < z0 + a.tz && t < a.nz) {
             // finished plane t: renormalise, pulse, store
-            const long long base = (long long)t * th.plane;
+            const int base = t * th.plane;
 #pragma unroll
             for (int rr = 0; rr < PY; ++rr) {
                 f2 ox = r.y[slot][rr][0], oy = r.y[slot][rr][1], oz = r.y[slot][rr][2];
@@ -369,7 +370,7 @@ __device__ __forceinline__ void patch_iteration(const PatchArgs& a, PRings<S, HS
                     // both columns of the pair are outputs or neither (even row
                     // length, even tile offsets): one 8-byte store per component
                     if (th.out[rr][0]) {
-                        const long long site = base + th.col[rr][0];
+                        const int site = base + th.col[rr][0];
                         *reinterpret_cast<f2*>(a.out0 + site) = ox;
                         *reinterpret_cast<f2*>(a.out1 + site) = oy;
                         *reinterpret_cast<f2*>(a.out2 + site) = oz;
@@ -380,7 +381,7 @@ __device__ __forceinline__ void patch_iteration(const PatchArgs& a, PRings<S, HS
 #pragma unroll
                 for (int e = 0; e < 2; ++e) {
                     if (!th.out[rr][e]) continue;
-                    const long long site = base + th.col[rr][e];
+                    const int site = base + th.col[rr][e];
                     if (PULSE) pulse_site<float>(vx[e], vy[e], vz[e], a.seed, (uint64_t)site, (uint64_t)k, a.replica, a.sigma);
                     a.out0[site] = vx[e];
                     a.out1[site] = vy[e];
@@ -400,7 +401,10 @@ __device__ __forceinline__ void patch_tile(const PatchArgs& a, int bx, int by, i
     PThread<PY> th;
     th.tx = threadIdx.x;
     th.ty = threadIdx.y;
-    th.warp_row = (threadIdx.y * kPT + threadIdx.x) >> 5;   // two thread rows per warp
+    // two thread rows per warp; broadcast from lane 0 so that the compiler
+    // knows the index (and every stage-activity test built on it) is
+    // warp-uniform and branches without divergence handling
+    th.warp_row = __shfl_sync(0xffffffffu, (int)((threadIdx.y * kPT + threadIdx.x) >> 5), 0);
     constexpr int OUTX = kPC - 2 * S, OUTY = ROWS - 2 * S;
     th.plane = a.nx * a.ny;
 #pragma unroll
@@ -438,10 +442,10 @@ __device__ __forceinline__ void patch_tile(const PatchArgs& a, int bx, int by, i
             }
 #pragma unroll
     for (int L = S - 2; L <= S - 1; ++L) {
-        const long long base = (long long)wrapi(t0 + L, a.nz) * th.plane;
+        const int base = wrapi(t0 + L, a.nz) * th.plane;
 #pragma unroll
         for (int rr = 0; rr < PY; ++rr) {
-            const long long o0 = base + th.col[rr][0], o1 = base + th.col[rr][1];
+            const int o0 = base + th.col[rr][0], o1 = base + th.col[rr][1];
             r.s[L & 3][rr][0] = make_float2(__ldg(a.in0 + o0), __ldg(a.in0 + o1));
             r.s[L & 3][rr][1] = make_float2(__ldg(a.in1 + o0), __ldg(a.in1 + o1));
             r.s[L & 3][rr][2] = make_float2(__ldg(a.in2 + o0), __ldg(a.in2 + o1));
@@ -637,6 +641,7 @@ PatchArgs patch_args_common(const StepLaunch<float>& L) {
     a.sigma = L.sigma;
     a.interval = L.d_interval;
     a.bc = L.bc;
+    a.err = L.d_status;
     return a;
 }
 
