@@ -19,6 +19,9 @@ CASES = [  # size, precision, integrator, precession, h_site, path
     ((20, 19, 18), 32, 2, 0, False, 0),
     ((20, 19, 18), 64, 1, 1, False, 0),
     ((11, 12, 7), 32, 0, 1, True, 1),
+    # rows of 64 / 128 columns: no spin beyond the first and last column
+    ((64, 19, 9), 32, 0, 1, False, 0),
+    ((128, 9, 11), 32, 0, 0, False, 0),
 ]
 
 

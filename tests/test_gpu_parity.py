@@ -59,6 +59,11 @@ CASES = [
     ((9, 10, 11), 64, 1, 0, False, 0),
     ((20, 19, 18), 64, 0, 1, True, 1),
     ((20, 19, 18), 32, 0, 0, False, 1),
+    # rows of 64 and 128 columns (2 and 4 tiles of the fused step along x,
+    # the benchmark's row length)
+    ((128, 10, 7), 32, 0, 1, False, 0),
+    ((64, 30, 21), 32, 0, 0, False, 0),
+    ((64, 17, 40), 32, 0, 1, False, 0),
 ]
 
 
