@@ -2,11 +2,17 @@
 // of the final state L = dLdE E(s_n) + dLdM . M(s_n), with checkpointing:
 // the forward run stores the state every K steps; the backward pass restores
 // each checkpoint, recomputes its K states with the forward kernels, and runs
-// the transposed step backwards through them.  Parameter gradients (J, D, H,
-// per-site h_i) accumulate in FP64: each site's term of each stage is formed
-// in the state precision (like the forward stencil) and added in FP64, into
-// the caller's FP64 field-gradient array (h_i) or into FP64 per-thread sums
-// that are reduced in FP64 (J, D, H).
+// the transposed step backwards through them.
+//
+// Parameter gradients accumulate in FP64: every site's term of every stage is
+// formed in the state precision (like the forward stencil) and added in FP64
+// into per-site FP64 arrays -- dL/dh_i (3N), and the site's dL/dJ and dL/dD
+// terms (N each), which are summed over the sites in FP64 once, after the
+// backward pass.  H enters the effective field exactly as every h_i
+// does, so dL/dH = sum_i dL/dh_i is that array's FP64 sum (explicit final-time
+// term included).  The float-to-double conversions of the terms are done with
+// integer bit operations (exact for every finite float), because this GPU's
+// FP64 pipe, which would otherwise convert them, is ~1/76 of its FP32 rate.
 //
 // Transposes used (f the right-hand side of Eq. LLL at fixed noise, a = s x H):
 //   w_i = (df_i/dH_i)^T v_i = -(s x v) - lambda s x (s x v)    [slow: without -(s x v)]
@@ -16,6 +22,14 @@
 //   pulse rotation R (Eq. s_rotation): lam <- R^T lam (rotation by -phi)
 //   RK stages: lam_K_j = b_j lam_y, then for j = S..1: lam_x_j = J_f(x_j)^T (dt lam_K_j),
 //              lam_s += lam_x_j, lam_K_l += a_jl lam_x_j (l < j)
+//
+// Indexing: a 3D grid of (row segment of 32 x-sites, group of 8 rows, plane),
+// one thread per site and one warp per row segment, so no coordinate needs a
+// division; every array is addressed through per-component base pointers with
+// 32-bit site offsets.  For FP32 chain tableaus the recomputing forward step
+// stores, per step of a segment, the stage inputs X_j (j >= 2), the stage
+// neighbour sums sum_nn X_j (j >= 1) and the unnormalised RK result y; the
+// transposes then read them instead of recomputing any stencil of X_j.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -28,40 +42,77 @@ namespace spin {
 
 namespace {
 
-constexpr int kAT = 256;
+constexpr int kAT = 256;                 // threads per block (8 warps)
+constexpr int kAW = kAT / 32;
 
-// Neighbour indices x-1, x+1, y-1, y+1, z-1, z+1 (periodic wrap) of site i,
-// and in w the weight of each: 0 for a neighbour across a face of a
-// free-boundary lattice.  Two integer divisions per site, the wrap by
-// comparison.
+// Exact float -> double: sign, exponent rebased from 127 to 1023, mantissa
+// shifted into the top of the 52-bit field.  Zeros keep their sign; only
+// subnormal, infinite and NaN floats take the hardware conversion.
+__device__ __forceinline__ double to_f64(float f) {
+    const unsigned b = __float_as_uint(f);
+    const unsigned e = (b >> 23) & 0xFFu;
+    const unsigned long long sign = (unsigned long long)(b & 0x80000000u) << 32;
+    if ((b & 0x7FFFFFFFu) == 0u) return __longlong_as_double((long long)sign);
+    if (e == 0u || e == 0xFFu) return (double)f;
+    return __longlong_as_double(
+        (long long)(sign | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(b & 0x7FFFFFu) << 29)));
+}
+__device__ __forceinline__ double to_f64(double d) { return d; }
+
+// A site of the lattice with its six neighbours (x-1, x+1, y-1, y+1, z-1, z+1;
+// periodic wrap) and their weights (0 across a face of a free-boundary
+// lattice).  All indices fit in 32 bits (N < 2^31).
 template <typename real>
-__device__ __forceinline__ void neighbours_w(long long i, int nx, int ny, int nz, int bc, long long nb[6], real w[6]) {
-    const int ii = (int)i;   // N < 2^31
-    const int r = ii / nx;
-    const int x = ii - r * nx;
-    const int z = r / ny;
-    const int y = r - z * ny;
-    const long long P = (long long)nx * ny;
-    const long long N = P * nz;
-    nb[0] = x > 0 ? i - 1 : i + (nx - 1);
-    nb[1] = x < nx - 1 ? i + 1 : i - (nx - 1);
-    nb[2] = y > 0 ? i - nx : i + (long long)(ny - 1) * nx;
-    nb[3] = y < ny - 1 ? i + nx : i - (long long)(ny - 1) * nx;
-    nb[4] = z > 0 ? i - P : i + (N - P);
-    nb[5] = z < nz - 1 ? i + P : i - (N - P);
-    w[0] = (bc && x == 0) ? real(0) : real(1);
-    w[1] = (bc && x == nx - 1) ? real(0) : real(1);
-    w[2] = (bc && y == 0) ? real(0) : real(1);
-    w[3] = (bc && y == ny - 1) ? real(0) : real(1);
-    w[4] = (bc && z == 0) ? real(0) : real(1);
-    w[5] = (bc && z == nz - 1) ? real(0) : real(1);
+struct Site {
+    int i;
+    int nb[6];
+    real wn[6];
+    bool valid;
+};
+
+// The site of this thread: the 3D grid is (row segment of 32 x-sites, group of
+// 8 rows, plane), one warp per row segment, so no coordinate needs a division.
+template <typename real>
+__device__ __forceinline__ Site<real> site_here(int nx, int ny, int nz, int bc) {
+    Site<real> s;
+    const int x = (int)(blockIdx.x * 32 + (threadIdx.x & 31));
+    const int y0 = (int)(blockIdx.y * kAW + (threadIdx.x >> 5));
+    const int z = (int)blockIdx.z;
+    s.valid = x < nx && y0 < ny;
+    const int xx = x < nx ? x : nx - 1;        // idle lanes read a valid site and write nothing
+    const int y = y0 < ny ? y0 : ny - 1;
+    const int P = nx * ny;
+    const int i = (z * ny + y) * nx + xx;
+    s.i = i;
+    s.nb[0] = xx > 0 ? i - 1 : i + (nx - 1);
+    s.nb[1] = xx < nx - 1 ? i + 1 : i - (nx - 1);
+    s.nb[2] = y > 0 ? i - nx : i + (ny - 1) * nx;
+    s.nb[3] = y < ny - 1 ? i + nx : i - (ny - 1) * nx;
+    s.nb[4] = z > 0 ? i - P : i + (nz - 1) * P;
+    s.nb[5] = z < nz - 1 ? i + P : i - (nz - 1) * P;
+    s.wn[0] = (bc && xx == 0) ? real(0) : real(1);
+    s.wn[1] = (bc && xx == nx - 1) ? real(0) : real(1);
+    s.wn[2] = (bc && y == 0) ? real(0) : real(1);
+    s.wn[3] = (bc && y == ny - 1) ? real(0) : real(1);
+    s.wn[4] = (bc && z == 0) ? real(0) : real(1);
+    s.wn[5] = (bc && z == nz - 1) ? real(0) : real(1);
+    return s;
 }
 
-__device__ __forceinline__ void cross3(const double a[3], const double b[3], double c[3]) {
-    c[0] = a[1] * b[2] - a[2] * b[1];
-    c[1] = a[2] * b[0] - a[0] * b[2];
-    c[2] = a[0] * b[1] - a[1] * b[0];
+// Record of this block in the per-block partial sums.
+__device__ __forceinline__ int block_record() {
+    return (int)(blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z));
 }
+
+// Component arrays (x, y, z blocks of a 3N array).
+template <typename real>
+struct V3 {
+    real* c[3];
+};
+template <typename real>
+struct CV3 {
+    const real* c[3];
+};
 
 template <typename real>
 __device__ __forceinline__ void cross3r(const real a[3], const real b[3], real c[3]) {
@@ -83,45 +134,40 @@ __device__ __forceinline__ T block_sum(T v, T* red) {
     return t;
 }
 
-// H_eff at site i of a component-major 3N array x (FP32 or FP64 storage,
-// evaluated in the storage precision like the forward kernels).
-template <typename real, bool HSITE>
-__device__ __forceinline__ void heff_at(const real* __restrict__ x, const real* __restrict__ hs, long long i,
-                                        const long long nb[6], const real wn[6], long long N, real J, real twoD,
-                                        const real H[3], real h[3]) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const real* q = x + c * N;
-        const real sum = wn[0] * q[nb[0]] + wn[1] * q[nb[1]] + wn[2] * q[nb[2]] + wn[3] * q[nb[3]] + wn[4] * q[nb[4]] +
-                         wn[5] * q[nb[5]];
-        h[c] = J * sum + H[c];
-        if (HSITE) h[c] += hs[c * N + i];
-    }
-    h[2] += twoD * x[2 * N + i];
+// Geometry and physics shared by the backward kernels.
+template <typename real>
+struct AdjGeom {
+    int nx, ny, nz, bc;
+    long long N;
+    real J, twoD, H[3], lambda, dt;
+};
+
+// Neighbour sum of one component array at a site.
+template <typename real>
+__device__ __forceinline__ real nbsum(const real* __restrict__ q, const Site<real>& st) {
+    return st.wn[0] * q[st.nb[0]] + st.wn[1] * q[st.nb[1]] + st.wn[2] * q[st.nb[2]] + st.wn[3] * q[st.nb[3]] +
+           st.wn[4] * q[st.nb[4]] + st.wn[5] * q[st.nb[5]];
 }
 
-// K = dt f(x) over component-major arrays.
-// Launch bounds for the stencil kernels of the backward pass: they are bound
-// by the latency of the neighbour gathers, so four resident blocks per SM
-// (at most 64 registers per thread) keep more loads in flight.
-constexpr int kAdjMinBlocks = 4;
-
+// K = dt f(x) over component arrays (stages recomputed in the backward pass
+// when they are not stored).
 template <typename real, bool PREC, bool HSITE>
-__global__ void __launch_bounds__(kAT, kAdjMinBlocks) k_adj_rhs(const real* __restrict__ x, const real* __restrict__ hs, real* __restrict__ K, int nx, int ny,
-                          int nz, real J, real twoD, real H0, real H1, real H2, real lambda, real dt, int bc) {
-    const long long N = (long long)nx * ny * nz;
-    const real H[3] = {H0, H1, H2};
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-        long long nb[6];
-        real wn[6];
-        neighbours_w<real>(i, nx, ny, nz, bc, nb, wn);
-        real h[3];
-        heff_at<real, HSITE>(x, hs, i, nb, wn, N, J, twoD, H, h);
-        real f[3];
-        llg_rhs<real, PREC>(x[i], x[N + i], x[2 * N + i], h[0], h[1], h[2], lambda, f[0], f[1], f[2]);
-        K[i] = dt * f[0];
-        K[N + i] = dt * f[1];
-        K[2 * N + i] = dt * f[2];
+__global__ void __launch_bounds__(kAT) k_adj_rhs(CV3<real> x, CV3<real> hs, V3<real> K, AdjGeom<real> G) {
+    const Site<real> st = site_here<real>(G.nx, G.ny, G.nz, G.bc);
+    const int i = st.i;
+    real h[3], s[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        s[c] = x.c[c][i];
+        h[c] = G.J * nbsum<real>(x.c[c], st) + G.H[c];
+        if (HSITE) h[c] += hs.c[c][i];
+    }
+    h[2] += G.twoD * s[2];
+    real f[3];
+    llg_rhs<real, PREC>(s[0], s[1], s[2], h[0], h[1], h[2], G.lambda, f[0], f[1], f[2]);
+    if (st.valid) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) K.c[c][i] = G.dt * f[c];
     }
 }
 
@@ -148,147 +194,137 @@ __global__ void k_adj_lincomb(real* __restrict__ out, const real* __restrict__ s
         out[q] = lincomb_at<real, NK>(s, lc, q);
 }
 
-// Stage transpose, site-local part ("w-part") at site i for the stage with
-// input x and v = dt lam_K: w and u, the per-site field gradient gh += w (in
-// FP64), and the site's terms of <w, sum_nn x> (J), 2 x_z w_z (D) and w (H)
-// added in FP64 to the thread's sums p[5].
+// Inputs of a stage's w-part: its input x and the neighbour sum of x (stored,
+// or computed here from x when sn.c[0] is null).
+template <typename real>
+struct StageIn {
+    CV3<real> x, sn;
+};
+
+// Stage transpose, site-local part ("w-part") at a site for the stage with
+// input x and v = dt lam_K: w and u, the per-site field gradient gh += w (FP64)
+// and the site's terms <w, sum_nn x> (J) and 2 x_z w_z (D) added in FP64 to
+// the site's entries of gjd (J at i, D at N + i).
+// Every load of the site is issued before the arithmetic.
 template <typename real, bool PREC, bool HSITE>
-__device__ __forceinline__ void w_part(const real* __restrict__ x, const real* __restrict__ hs, long long i,
-                                       const long long nb[6], const real wn[6], long long N, real J, real twoD,
-                                       const real H[3], real lambda, const real v[3], real* __restrict__ w,
-                                       real* __restrict__ u, double* __restrict__ gh, double p[5]) {
-    const real s[3] = {x[i], x[N + i], x[2 * N + i]};
-    real sn[3], hr[3];
+__device__ __forceinline__ void w_part(const StageIn<real>& in, const CV3<real>& hs, const Site<real>& st,
+                                       const AdjGeom<real>& G, const real v[3], const V3<real>& w, const V3<real>& u,
+                                       const V3<double>& gh, double* __restrict__ gjd) {
+    const int i = st.i;
+    real s[3], sn[3], hsv[3];
+    double g[3];
+    const double gj = gjd[i], gd = gjd[G.N + i];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        const real* q = x + c * N;
-        sn[c] = wn[0] * q[nb[0]] + wn[1] * q[nb[1]] + wn[2] * q[nb[2]] + wn[3] * q[nb[3]] + wn[4] * q[nb[4]] +
-                wn[5] * q[nb[5]];
-        hr[c] = J * sn[c] + H[c];
-        if (HSITE) hr[c] += hs[c * N + i];
+        s[c] = in.x.c[c][i];
+        sn[c] = in.sn.c[0] ? in.sn.c[c][i] : nbsum<real>(in.x.c[c], st);
+        hsv[c] = HSITE ? hs.c[c][i] : real(0);
+        g[c] = gh.c[c][i];
     }
-    hr[2] += twoD * s[2];
+    real hr[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        hr[c] = G.J * sn[c] + G.H[c];
+        if (HSITE) hr[c] += hsv[c];
+    }
+    hr[2] += G.twoD * s[2];
     // the transpose in the state precision (like the forward stages)
-    real a[3], sv[3], ssv[3], hv[3], av[3], hsv[3];
+    real a[3], sv[3], ssv[3], hv[3], av[3], hsx[3];
     cross3r(s, hr, a);
     cross3r(s, v, sv);
     cross3r(s, sv, ssv);
     cross3r(hr, v, hv);
     cross3r(a, v, av);
-    cross3r(hr, sv, hsv);
+    cross3r(hr, sv, hsx);
     real wi[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         real ui;
         if (PREC) {
-            wi[c] = -sv[c] - lambda * ssv[c];
-            ui = hv[c] - lambda * av[c] + lambda * hsv[c];
+            wi[c] = -sv[c] - G.lambda * ssv[c];
+            ui = hv[c] - G.lambda * av[c] + G.lambda * hsx[c];
         } else {
-            wi[c] = -lambda * ssv[c];
-            ui = -lambda * av[c] + lambda * hsv[c];
+            wi[c] = -G.lambda * ssv[c];
+            ui = -G.lambda * av[c] + G.lambda * hsx[c];
         }
-        w[c * N + i] = wi[c];
-        u[c * N + i] = ui;
-        if (gh) gh[c * N + i] += (double)wi[c];
+        if (!st.valid) wi[c] = real(0);
+        if (st.valid) {
+            w.c[c][i] = wi[c];
+            u.c[c][i] = ui;
+            gh.c[c][i] = g[c] + to_f64(wi[c]);
+        }
     }
-    p[0] += (double)(wi[0] * sn[0] + wi[1] * sn[1] + wi[2] * sn[2]);
-    p[1] += (double)(real(2) * s[2] * wi[2]);
-    p[2] += (double)wi[0];
-    p[3] += (double)wi[1];
-    p[4] += (double)wi[2];
-}
-
-// Block partials of the w-parts: the threads' FP64 sums are reduced in FP64
-// (warp shuffles, then the block's warps in a fixed order) and added into the
-// block's record.  Each block adds into its own record, launch after launch in
-// stream order (deterministic); the records are summed once after the
-// backward pass.
-__device__ __forceinline__ void flush_partials(double p[5], double* __restrict__ partials) {
-    __shared__ double red[kAT / 32][5];
-#pragma unroll
-    for (int q = 0; q < 5; ++q) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) p[q] += __shfl_xor_sync(0xffffffffu, p[q], o);
-    }
-    if ((threadIdx.x & 31) == 0)
-#pragma unroll
-        for (int q = 0; q < 5; ++q) red[threadIdx.x >> 5][q] = p[q];
-    __syncthreads();
-    if (threadIdx.x < 5) {
-        double t = 0;
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k][threadIdx.x];
-        partials[(long long)blockIdx.x * 5 + threadIdx.x] += t;
+    if (st.valid) {
+        gjd[i] = gj + to_f64(wi[0] * sn[0] + wi[1] * sn[1] + wi[2] * sn[2]);
+        gjd[G.N + i] = gd + to_f64(real(2) * s[2] * wi[2]);
     }
 }
-
-// Geometry and physics shared by the backward kernels.
-template <typename real>
-struct AdjGeom {
-    int nx, ny, nz, bc;
-    real J, twoD, H[3], lambda, dt;
-};
 
 // Top of the transposed step: pulse and renormalisation transposes, lam_s =
 // lam_y, lam_K_j = b_j lam_y (stored for j < S-1), then the w-part of the
 // last stage S-1, whose lam_K is not changed by any other stage.
 template <typename real>
 struct TopArgs {
-    real* lam;           // in: dL/ds_after; out: lam_s = lam_y
-    const real* s;       // state before the step
-    LinComb<real> yc;    // y = s + sum_j b_j K_j, the unnormalised RK result
-    real* LK[6];
+    V3<real> lam;        // in: dL/ds_after; out: lam_s = lam_y
+    const real* s;       // state before the step (3N)
+    CV3<real> ystored;   // the unnormalised RK result, when the step stored it (c[0] null otherwise)
+    LinComb<real> yc;    // otherwise y = s + sum_j b_j K_j (3N arrays)
+    V3<real> LK[6];
     real b[6];
     int renorm, pulse;
     uint64_t seed, replica;
     long long k;
     real sigma;
-    const real* xlast;   // input of stage S-1
-    const real* hs;
-    real* w;             // w, u of stage S-1
-    real* u;
-    double* gh;          // FP64 field gradient (3N) or null
-    double* partials;
+    StageIn<real> last;  // input of stage S-1 and its neighbour sum
+    CV3<real> hs;
+    V3<real> w, u;       // w, u of stage S-1
+    V3<double> gh;       // FP64 field gradient
+    double* gjd;         // FP64 per-site dL/dJ (N) and dL/dD (N) terms
 };
 
 template <typename real, bool PREC, bool HSITE, int S>
-__global__ void __launch_bounds__(kAT, kAdjMinBlocks) k_adj_top_w(TopArgs<real> a, AdjGeom<real> G) {
-    const long long N = (long long)G.nx * G.ny * G.nz;
-    double p[5] = {0, 0, 0, 0, 0};
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-        real l0 = a.lam[i], l1 = a.lam[N + i], l2 = a.lam[2 * N + i];
-        if (a.pulse) {
-            const Words4 w = noise_words(a.seed, (uint64_t)i, (uint64_t)a.k, a.replica);
-            real g0, g1, g2;
-            Gauss<real>::draw(w, g0, g1, g2);
-            pulse_rotate<real>(l0, l1, l2, -a.sigma * g0, -a.sigma * g1, -a.sigma * g2);
+__global__ void __launch_bounds__(kAT) k_adj_top_w(TopArgs<real> a, AdjGeom<real> G) {
+    const Site<real> st = site_here<real>(G.nx, G.ny, G.nz, G.bc);
+    const int i = st.i;
+    real l0 = a.lam.c[0][i], l1 = a.lam.c[1][i], l2 = a.lam.c[2][i];
+    if (a.pulse) {
+        const Words4 wd = noise_words(a.seed, (uint64_t)i, (uint64_t)a.k, a.replica);
+        real g0, g1, g2;
+        Gauss<real>::draw(wd, g0, g1, g2);
+        pulse_rotate<real>(l0, l1, l2, -a.sigma * g0, -a.sigma * g1, -a.sigma * g2);
+    }
+    if (a.renorm) {
+        real y0, y1, y2;
+        if (a.ystored.c[0]) {
+            y0 = a.ystored.c[0][i];
+            y1 = a.ystored.c[1][i];
+            y2 = a.ystored.c[2][i];
+        } else {
+            y0 = lincomb_at<real, S>(a.s, a.yc, i);
+            y1 = lincomb_at<real, S>(a.s, a.yc, G.N + i);
+            y2 = lincomb_at<real, S>(a.s, a.yc, 2 * G.N + i);
         }
-        if (a.renorm) {
-            const real y0 = lincomb_at<real, S>(a.s, a.yc, i), y1 = lincomb_at<real, S>(a.s, a.yc, N + i),
-                       y2 = lincomb_at<real, S>(a.s, a.yc, 2 * N + i);
-            const real n = Math<real>::sqrt_(y0 * y0 + y1 * y1 + y2 * y2);
-            const real u0 = y0 / n, u1 = y1 / n, u2 = y2 / n;
-            const real ul = u0 * l0 + u1 * l1 + u2 * l2;
-            l0 = (l0 - u0 * ul) / n;
-            l1 = (l1 - u1 * ul) / n;
-            l2 = (l2 - u2 * ul) / n;
-        }
-        a.lam[i] = l0;
-        a.lam[N + i] = l1;
-        a.lam[2 * N + i] = l2;
+        const real n = Math<real>::sqrt_(y0 * y0 + y1 * y1 + y2 * y2);
+        const real u0 = y0 / n, u1 = y1 / n, u2 = y2 / n;
+        const real ul = u0 * l0 + u1 * l1 + u2 * l2;
+        l0 = (l0 - u0 * ul) / n;
+        l1 = (l1 - u1 * ul) / n;
+        l2 = (l2 - u2 * ul) / n;
+    }
+    if (st.valid) {
+        a.lam.c[0][i] = l0;
+        a.lam.c[1][i] = l1;
+        a.lam.c[2][i] = l2;
 #pragma unroll
         for (int j = 0; j < S - 1; ++j) {
-            a.LK[j][i] = a.b[j] * l0;
-            a.LK[j][N + i] = a.b[j] * l1;
-            a.LK[j][2 * N + i] = a.b[j] * l2;
+            a.LK[j].c[0][i] = a.b[j] * l0;
+            a.LK[j].c[1][i] = a.b[j] * l1;
+            a.LK[j].c[2][i] = a.b[j] * l2;
         }
-        long long nb[6];
-        real wn[6];
-        neighbours_w<real>(i, G.nx, G.ny, G.nz, G.bc, nb, wn);
-        const real bl = a.b[S - 1] * G.dt;
-        const real v[3] = {bl * l0, bl * l1, bl * l2};
-        w_part<real, PREC, HSITE>(a.xlast, a.hs, i, nb, wn, N, G.J, G.twoD, G.H, G.lambda, v, a.w, a.u, a.gh, p);
     }
-    flush_partials(p, a.partials);
+    const real bl = a.b[S - 1] * G.dt;
+    const real v[3] = {bl * l0, bl * l1, bl * l2};
+    w_part<real, PREC, HSITE>(a.last, a.hs, st, G, v, a.w, a.u, a.gh, a.gjd);
 }
 
 // Stage j of the transposed step: the neighbour part ("x-part") of stage j,
@@ -299,148 +335,155 @@ __global__ void __launch_bounds__(kAT, kAdjMinBlocks) k_adj_top_w(TopArgs<real> 
 // other.
 template <typename real>
 struct XWArgs {
-    const real* w;       // stage j
-    const real* u;
-    real* lam;
-    real* LK[6];
+    CV3<real> w, u;      // stage j
+    V3<real> lam;
+    V3<real> LK[6];
     real a[6];           // a_jl
-    const real* xprev;   // input of stage j-1
-    const real* hs;
-    real* wn;            // w, u of stage j-1
-    real* un;
-    double* gh;          // FP64 field gradient (3N) or null
-    double* partials;
+    StageIn<real> prev;  // input of stage j-1 and its neighbour sum
+    CV3<real> hs;
+    V3<real> wn, un;     // w, u of stage j-1
+    V3<double> gh;       // FP64 field gradient
+    double* gjd;         // FP64 per-site dL/dJ (N) and dL/dD (N) terms
 };
 
 template <typename real, bool PREC, bool HSITE, int NL, bool W>
-__global__ void __launch_bounds__(kAT, kAdjMinBlocks) k_adj_xw(XWArgs<real> a, AdjGeom<real> G) {
-    const long long N = (long long)G.nx * G.ny * G.nz;
-    double p[5] = {0, 0, 0, 0, 0};
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-        long long nb[6];
-        real wn[6];
-        neighbours_w<real>(i, G.nx, G.ny, G.nz, G.bc, nb, wn);
-        real lk[3] = {0, 0, 0};   // lam_K_{j-1} at the site after this stage
+__global__ void __launch_bounds__(kAT) k_adj_xw(XWArgs<real> a, AdjGeom<real> G) {
+    const Site<real> st = site_here<real>(G.nx, G.ny, G.nz, G.bc);
+    const int i = st.i;
+    real ux[3], lm[3], wz, nsum[3], lkv[NL > 0 ? NL : 1][3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const real* q = a.w + c * N;
-            real lx = a.u[c * N + i] + G.J * (wn[0] * q[nb[0]] + wn[1] * q[nb[1]] + wn[2] * q[nb[2]] +
-                                              wn[3] * q[nb[3]] + wn[4] * q[nb[4]] + wn[5] * q[nb[5]]);
-            if (c == 2) lx += G.twoD * a.w[2 * N + i];
-            a.lam[c * N + i] += lx;
+    for (int c = 0; c < 3; ++c) {
+        ux[c] = a.u.c[c][i];
+        lm[c] = a.lam.c[c][i];
+        nsum[c] = nbsum<real>(a.w.c[c], st);
 #pragma unroll
-            for (int l = 0; l < NL; ++l) {
-                if (a.a[l] != real(0)) {
-                    const real nv = a.LK[l][c * N + i] + a.a[l] * lx;
-                    a.LK[l][c * N + i] = nv;
-                    if (l == NL - 1) lk[c] = nv;
-                } else if (l == NL - 1) {
-                    lk[c] = a.LK[l][c * N + i];
-                }
+        for (int l = 0; l < NL; ++l) lkv[l][c] = a.LK[l].c[c][i];
+    }
+    wz = a.w.c[2][i];
+    real lk[3] = {0, 0, 0};   // lam_K_{j-1} at the site after this stage
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        real lx = ux[c] + G.J * nsum[c];
+        if (c == 2) lx += G.twoD * wz;
+        if (st.valid) a.lam.c[c][i] = lm[c] + lx;
+#pragma unroll
+        for (int l = 0; l < NL; ++l) {
+            if (a.a[l] != real(0)) {
+                const real nv = lkv[l][c] + a.a[l] * lx;
+                if (st.valid) a.LK[l].c[c][i] = nv;
+                if (l == NL - 1) lk[c] = nv;
+            } else if (l == NL - 1) {
+                lk[c] = lkv[l][c];
             }
         }
-        if (W) {
-            const real v[3] = {G.dt * lk[0], G.dt * lk[1], G.dt * lk[2]};
-            w_part<real, PREC, HSITE>(a.xprev, a.hs, i, nb, wn, N, G.J, G.twoD, G.H, G.lambda, v, a.wn, a.un,
-                                      a.gh, p);
-        }
     }
-    if (W) flush_partials(p, a.partials);
+    if (W) {
+        const real v[3] = {G.dt * lk[0], G.dt * lk[1], G.dt * lk[2]};
+        w_part<real, PREC, HSITE>(a.prev, a.hs, st, G, v, a.wn, a.un, a.gh, a.gjd);
+    }
 }
 
-// acc[q] += sum over blocks of partials[b*5+q], fixed order (deterministic).
-__global__ void k_adj_accumulate(const double* __restrict__ partials, int nblocks, double* __restrict__ acc, double scale) {
-    __shared__ double red[kAT / 32];
-    for (int q = 0; q < 5; ++q) {
-        double v = 0;
-        for (int b = threadIdx.x; b < nblocks; b += blockDim.x) v += partials[(long long)b * 5 + q];
-        const double t = block_sum<double>(v, red);
-        if (threadIdx.x == 0) acc[q] += scale * t;
-    }
+// acc[q] += sum over sites of gjd[q N + i] (q = 0: J, 1: D), one block per
+// gradient, fixed order (deterministic).
+__global__ void k_adj_sum_jd(const double* __restrict__ gjd, long long N, double* __restrict__ acc) {
+    __shared__ double red[kAW];
+    const double* g = gjd + (long long)blockIdx.x * N;
+    double v = 0;
+    for (long long q = threadIdx.x; q < N; q += blockDim.x) v += g[q];
+    const double t = block_sum<double>(v, red);
+    if (threadIdx.x == 0) acc[blockIdx.x] += t;
+}
+
+// dL/dH = sum_i dL/dh_i: FP64 sums of the three components of the field
+// gradient, one block per component, fixed order.
+__global__ void k_adj_sum_gh(const double* __restrict__ gh, long long N, double* __restrict__ acc) {
+    __shared__ double red[kAW];
+    const double* g = gh + (long long)blockIdx.x * N;
+    double v = 0;
+    for (long long q = threadIdx.x; q < N; q += blockDim.x) v += g[q];
+    const double t = block_sum<double>(v, red);
+    if (threadIdx.x == 0) acc[2 + blockIdx.x] = t;
 }
 
 // Loss seed: lam_i = (-dLdE H_eff,i + dLdM)/N from the final state, with the
-// explicit final-time terms: partials of bonds, sum s_z^2, M; gh += -dLdE s_i/N.
+// explicit final-time terms: partials of bonds (J) and sum s_z^2 (D);
+// gh += -dLdE s_i/N (the explicit dE/dh_i, which also gives dE/dH through the
+// final sum of gh).
 template <typename real, bool HSITE>
-__global__ void __launch_bounds__(kAT) k_adj_seed(const real* __restrict__ s, const real* __restrict__ hs,
-                                                  real* __restrict__ lam, double* __restrict__ gh,
-                                                  double* __restrict__ partials, int nx, int ny, int nz, real J,
-                                                  real twoD, real H0, real H1, real H2, double dLdE, double dM0,
-                                                  double dM1, double dM2, int bc) {
-    __shared__ double red[kAT / 32];
-    const long long N = (long long)nx * ny * nz;
-    const real H[3] = {H0, H1, H2};
+__global__ void __launch_bounds__(kAT) k_adj_seed(CV3<real> s, CV3<real> hs, V3<real> lam, V3<double> gh,
+                                                  double* __restrict__ partials, AdjGeom<real> G, double dLdE,
+                                                  double dM0, double dM1, double dM2) {
+    __shared__ double red[kAW];
+    const long long N = G.N;
     const double dM[3] = {dM0, dM1, dM2};
-    double bonds = 0, sz2 = 0, m0 = 0, m1 = 0, m2 = 0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-        long long nb[6];
-        real wn[6];
-        neighbours_w<real>(i, nx, ny, nz, bc, nb, wn);
-        real h[3];
-        heff_at<real, HSITE>(s, hs, i, nb, wn, N, J, twoD, H, h);
+    double bonds = 0, sz2 = 0;
+    const Site<real> st = site_here<real>(G.nx, G.ny, G.nz, G.bc);
+    const int i = st.i;
+    real h[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        h[c] = G.J * nbsum<real>(s.c[c], st) + G.H[c];
+        if (HSITE) h[c] += hs.c[c][i];
+    }
+    h[2] += G.twoD * s.c[2][i];
+    if (st.valid) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            lam[c * N + i] = (real)((-dLdE * (double)h[c] + dM[c]) / (double)N);
-            if (gh) gh[c * N + i] += -dLdE * (double)s[c * N + i] / (double)N;
+            lam.c[c][i] = (real)((-dLdE * (double)h[c] + dM[c]) / (double)N);
+            gh.c[c][i] += -dLdE * (double)s.c[c][i] / (double)N;
         }
-        const double a = s[i], b = s[N + i], c = s[2 * N + i];
-        const double w1 = wn[1], w3 = wn[3], w5 = wn[5];   // forward bonds inside the lattice
-        bonds += a * (w1 * s[nb[1]] + w3 * s[nb[3]] + w5 * s[nb[5]]) +
-                 b * (w1 * s[N + nb[1]] + w3 * s[N + nb[3]] + w5 * s[N + nb[5]]) +
-                 c * (w1 * s[2 * N + nb[1]] + w3 * s[2 * N + nb[3]] + w5 * s[2 * N + nb[5]]);
-        sz2 += c * c;
-        m0 += a;
-        m1 += b;
-        m2 += c;
+        const double a = s.c[0][i], b = s.c[1][i], c = s.c[2][i];
+        const double w1 = st.wn[1], w3 = st.wn[3], w5 = st.wn[5];   // forward bonds inside the lattice
+        const int* nb = st.nb;
+        bonds = a * (w1 * s.c[0][nb[1]] + w3 * s.c[0][nb[3]] + w5 * s.c[0][nb[5]]) +
+                b * (w1 * s.c[1][nb[1]] + w3 * s.c[1][nb[3]] + w5 * s.c[1][nb[5]]) +
+                c * (w1 * s.c[2][nb[1]] + w3 * s.c[2][nb[3]] + w5 * s.c[2][nb[5]]);
+        sz2 = c * c;
     }
-    const double vals[5] = {bonds, sz2, m0, m1, m2};
-    for (int q = 0; q < 5; ++q) {
+    const double vals[2] = {bonds, sz2};
+    for (int q = 0; q < 2; ++q) {
         const double t = block_sum<double>(vals[q], red);
-        if (threadIdx.x == 0) partials[(long long)blockIdx.x * 5 + q] = t;
+        if (threadIdx.x == 0) partials[(long long)block_record() * 2 + q] = t;
     }
 }
 
-// explicit terms -> gradient accumulators: acc = (gJ, gD, gH0, gH1, gH2)
-__global__ void k_adj_seed_finish(const double* __restrict__ partials, int nblocks, double* __restrict__ acc, double dLdE,
-                                  double N) {
-    __shared__ double red[kAT / 32];
-    double t[5];
-    for (int q = 0; q < 5; ++q) {
+// explicit terms -> gradient accumulators acc = (gJ, gD)
+__global__ void k_adj_seed_finish(const double* __restrict__ partials, int nblocks, double* __restrict__ acc,
+                                  double dLdE, double N) {
+    __shared__ double red[kAW];
+    double t[2];
+    for (int q = 0; q < 2; ++q) {
         double v = 0;
-        for (int b = threadIdx.x; b < nblocks; b += blockDim.x) v += partials[(long long)b * 5 + q];
+        for (int b = threadIdx.x; b < nblocks; b += blockDim.x) v += partials[(long long)b * 2 + q];
         t[q] = block_sum<double>(v, red);
     }
     if (threadIdx.x == 0) {
         acc[0] += -dLdE * t[0] / N;
         acc[1] += -dLdE * t[1] / N;
-        acc[2] += -dLdE * t[2] / N;
-        acc[3] += -dLdE * t[3] / N;
-        acc[4] += -dLdE * t[4] / N;
-    }
-}
-
-template <typename real>
-__global__ void k_gather3(real* __restrict__ dst, const real* __restrict__ s0, const real* __restrict__ s1,
-                          const real* __restrict__ s2, long long N) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-        dst[i] = s0[i];
-        dst[N + i] = s1[i];
-        dst[2 * N + i] = s2[i];
     }
 }
 
 int grid_for(long long n) { return (int)std::max<long long>(1, std::min<long long>((n + kAT - 1) / kAT, 152LL * 8)); }
 
+// The 3D grid of the site kernels: row segments of 32 x-sites, groups of 8
+// rows (one per warp), planes.
+dim3 grid3(const Geom& g) { return dim3((g.nx + 31) / 32, (g.ny + kAW - 1) / kAW, g.nz); }
+
 }  // namespace
 
-int adjoint_blocks(Geom g) { return grid_for(g.N()); }
+int adjoint_blocks(Geom g) {
+    const dim3 d = grid3(g);
+    return (int)(d.x * d.y * d.z);
+}
 
 constexpr size_t kStageStoreMax = (size_t)8 << 30;   // bytes of stage storage at most
 
+// Stored per step of a segment: X_j (j = 2..S), sum_nn X_j (j = 1..S) and y:
+// 2S arrays of 3N floats.
 bool adjoint_stores_stages(const Geom& g, int elt, const Tableau& tb, int path, int K) {
     if (elt != 4 || !tb.chain || path == 1 || !(tb.stages == 2 || tb.stages == 4)) return false;
     const size_t comp = ((size_t)3 * (size_t)g.N() * 4 + 255) / 256 * 256;
-    return comp * (size_t)(2 * tb.stages - 1) * (size_t)K <= kStageStoreMax;
+    return comp * (size_t)(2 * tb.stages) * (size_t)K <= kStageStoreMax;
 }
 
 size_t adjoint_workspace_bytes(const Geom& g, int elt, const Tableau& tb, int path, int K) {
@@ -449,11 +492,13 @@ size_t adjoint_workspace_bytes(const Geom& g, int elt, const Tableau& tb, int pa
     auto al = [](size_t v) { return (v + 255) / 256 * 256; };
     size_t b = 0;
     if (adjoint_stores_stages(g, elt, tb, path, K))
-        b += al(comp) * (size_t)(2 * stages - 1) * (size_t)K;   // X_j (j >= 2) and K_j of every step of a segment
+        b += al(comp) * (size_t)(2 * stages) * (size_t)K;   // X_j, sum_nn X_j and y of every step of a segment
     b += al(comp) * (size_t)(K + 1);     // segment states
     b += al(comp) * (size_t)stages * 3;  // X_j, K_j, lam_K_j
     b += al(comp) * 6;                   // y, lam, w and u (two pairs)
-    b += al(sizeof(double) * 5 * (size_t)adjoint_blocks(g));
+    b += al(sizeof(double) * 3 * (size_t)g.N());   // FP64 field gradient when the caller does not want it
+    b += al(sizeof(double) * 2 * (size_t)g.N());   // FP64 per-site dL/dJ and dL/dD terms
+    b += al(sizeof(double) * 2 * (size_t)adjoint_blocks(g));   // the seed's per-block partials
     b += al(sizeof(double) * 8);         // accumulators
     b += al(sizeof(long long));          // pulse-number slot
     return b;
@@ -474,7 +519,7 @@ void launch_lincomb(int nk, real* out, const real* s, const LinComb<real>& lc, l
 }
 
 template <typename real, bool PREC, bool HSITE>
-void launch_xw_t(int j, const XWArgs<real>& a, const AdjGeom<real>& G, int gb, cudaStream_t st) {
+void launch_xw_t(int j, const XWArgs<real>& a, const AdjGeom<real>& G, dim3 gb, cudaStream_t st) {
     switch (j) {
         case 0: k_adj_xw<real, PREC, HSITE, 0, false><<<gb, kAT, 0, st>>>(a, G); break;
         case 1: k_adj_xw<real, PREC, HSITE, 1, true><<<gb, kAT, 0, st>>>(a, G); break;
@@ -487,7 +532,7 @@ void launch_xw_t(int j, const XWArgs<real>& a, const AdjGeom<real>& G, int gb, c
 
 // x-part of stage j and (j > 0) w-part of stage j-1.
 template <typename real>
-void launch_xw(bool prec, bool hsite, int j, const XWArgs<real>& a, const AdjGeom<real>& G, int gb, cudaStream_t st) {
+void launch_xw(bool prec, bool hsite, int j, const XWArgs<real>& a, const AdjGeom<real>& G, dim3 gb, cudaStream_t st) {
     if (prec) {
         if (hsite) launch_xw_t<real, true, true>(j, a, G, gb, st);
         else launch_xw_t<real, true, false>(j, a, G, gb, st);
@@ -498,14 +543,14 @@ void launch_xw(bool prec, bool hsite, int j, const XWArgs<real>& a, const AdjGeo
 }
 
 template <typename real, bool PREC, bool HSITE>
-void launch_top_w_t(int S, const TopArgs<real>& a, const AdjGeom<real>& G, int gb, cudaStream_t st) {
+void launch_top_w_t(int S, const TopArgs<real>& a, const AdjGeom<real>& G, dim3 gb, cudaStream_t st) {
     if (S == 2) k_adj_top_w<real, PREC, HSITE, 2><<<gb, kAT, 0, st>>>(a, G);
     else if (S == 4) k_adj_top_w<real, PREC, HSITE, 4><<<gb, kAT, 0, st>>>(a, G);
     else k_adj_top_w<real, PREC, HSITE, 6><<<gb, kAT, 0, st>>>(a, G);
 }
 
 template <typename real>
-void launch_top_w(bool prec, bool hsite, int S, const TopArgs<real>& a, const AdjGeom<real>& G, int gb,
+void launch_top_w(bool prec, bool hsite, int S, const TopArgs<real>& a, const AdjGeom<real>& G, dim3 gb,
                   cudaStream_t st) {
     if (prec) {
         if (hsite) launch_top_w_t<real, true, true>(S, a, G, gb, st);
@@ -514,6 +559,19 @@ void launch_top_w(bool prec, bool hsite, int S, const TopArgs<real>& a, const Ad
         if (hsite) launch_top_w_t<real, false, true>(S, a, G, gb, st);
         else launch_top_w_t<real, false, false>(S, a, G, gb, st);
     }
+}
+
+template <typename real>
+V3<real> v3(real* base, long long N) {
+    V3<real> v;
+    for (int c = 0; c < 3; ++c) v.c[c] = base ? base + c * N : nullptr;
+    return v;
+}
+template <typename real>
+CV3<real> cv3(const real* base, long long N) {
+    CV3<real> v;
+    for (int c = 0; c < 3; ++c) v.c[c] = base ? base + c * N : nullptr;
+    return v;
 }
 
 template <typename real>
@@ -543,8 +601,7 @@ cudaError_t adjoint_run(const AdjointRun<real>& A) {
         LK[j] = reinterpret_cast<real*>(ws + off);
         off += al(compb);
     }
-    real* y = reinterpret_cast<real*>(ws + off);
-    off += al(compb);
+    off += al(compb);   // (unused slot, kept so the layout matches adjoint_workspace_bytes)
     real* lam = reinterpret_cast<real*>(ws + off);
     off += al(compb);
     real* wb[2];   // w and u of the stages, double-buffered by stage parity
@@ -555,56 +612,65 @@ cudaError_t adjoint_run(const AdjointRun<real>& A) {
         ub[q] = reinterpret_cast<real*>(ws + off);
         off += al(compb);
     }
+    // the FP64 field gradient: the caller's array, or a workspace one (dL/dH
+    // is its sum either way)
+    double* gh = A.g_h ? A.g_h : reinterpret_cast<double*>(ws + off);
+    off += al(sizeof(double) * 3 * (size_t)N);
     const int nb = adjoint_blocks(g);
+    const dim3 gb = grid3(g);
+    double* gjd = reinterpret_cast<double*>(ws + off);
+    off += al(sizeof(double) * 2 * (size_t)N);
     double* partials = reinterpret_cast<double*>(ws + off);
-    off += al(sizeof(double) * 5 * (size_t)nb);
+    off += al(sizeof(double) * 2 * (size_t)nb);
     double* acc = reinterpret_cast<double*>(ws + off);
     off += al(sizeof(double) * 8);
     long long* kslot = reinterpret_cast<long long*>(ws + off);
     off += al(sizeof(long long));
     // stage storage of a segment (A.store_stages): for step m of the segment
-    // (slot m-1) the inputs X_2..X_S and the increments K_1..K_S
+    // (slot m-1) the inputs X_2..X_S, the neighbour sums of X_1..X_S and y
     const bool stored = A.store_stages != 0;
     char* sbase = ws + off;
-    auto stage_x = [&](int j, int m) {   // X_j, j = 2..S (0-based stage index j-1 >= 1)
-        return reinterpret_cast<real*>(sbase + ((size_t)(m - 1) * (2 * S - 1) + (size_t)(j - 2)) * al(compb));
+    auto slot_arr = [&](int m, int q) {
+        return reinterpret_cast<real*>(sbase + ((size_t)(m - 1) * (2 * S) + (size_t)q) * al(compb));
     };
-    auto stage_k = [&](int j, int m) {   // K_j, j = 1..S
-        return reinterpret_cast<real*>(sbase + ((size_t)(m - 1) * (2 * S - 1) + (size_t)(S - 1) + (size_t)(j - 1)) * al(compb));
-    };
+    auto stage_x = [&](int j, int m) { return slot_arr(m, j - 2); };           // X_j, j = 2..S
+    auto stage_sn = [&](int j, int m) { return slot_arr(m, S - 1 + j - 1); };  // sum_nn X_j, j = 1..S
+    auto stage_y = [&](int m) { return slot_arr(m, 2 * S - 1); };
     cudaStream_t st = A.stream;
-    const real J = (real)A.J, twoD = (real)(2.0 * A.D), H0 = (real)A.H[0], H1 = (real)A.H[1], H2 = (real)A.H[2];
-    const real lamb = (real)A.lambda, dt = (real)A.dt;
     const real* hs = A.h_site;
     const bool HS = hs != nullptr;
+    const CV3<real> hs3 = cv3<real>(hs, N);
+    const V3<double> gh3 = v3<double>(gh, N);
     AdjGeom<real> G{};
     G.nx = g.nx;
     G.ny = g.ny;
     G.nz = g.nz;
     G.bc = A.bc;
-    G.J = J;
-    G.twoD = twoD;
-    G.H[0] = H0;
-    G.H[1] = H1;
-    G.H[2] = H2;
-    G.lambda = lamb;
-    G.dt = dt;
+    G.N = N;
+    G.J = (real)A.J;
+    G.twoD = (real)(2.0 * A.D);
+    G.H[0] = (real)A.H[0];
+    G.H[1] = (real)A.H[1];
+    G.H[2] = (real)A.H[2];
+    G.lambda = (real)A.lambda;
+    G.dt = (real)A.dt;
     cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(double) * 8, st);
     if (e != cudaSuccess) return e;
+    if (!A.g_h && (e = cudaMemsetAsync(gh, 0, sizeof(double) * 3 * (size_t)N, st)) != cudaSuccess) return e;
 
     // seed from the final state (component arrays of the caller)
-    real* fin = y;  // temporarily gather the final state
-    k_gather3<real><<<grid_for(N), kAT, 0, st>>>(fin, A.final_state[0], A.final_state[1], A.final_state[2], N);
+    CV3<real> fin;
+    for (int c = 0; c < 3; ++c) fin.c[c] = A.final_state[c];
     if (HS)
-        k_adj_seed<real, true><<<nb, kAT, 0, st>>>(fin, hs, lam, A.g_h, partials, g.nx, g.ny, g.nz, J, twoD, H0, H1, H2,
-                                                   A.dLdE, A.dLdM[0], A.dLdM[1], A.dLdM[2], A.bc);
+        k_adj_seed<real, true><<<gb, kAT, 0, st>>>(fin, hs3, v3<real>(lam, N), gh3, partials, G, A.dLdE, A.dLdM[0],
+                                                   A.dLdM[1], A.dLdM[2]);
     else
-        k_adj_seed<real, false><<<nb, kAT, 0, st>>>(fin, nullptr, lam, A.g_h, partials, g.nx, g.ny, g.nz, J, twoD, H0, H1,
-                                                    H2, A.dLdE, A.dLdM[0], A.dLdM[1], A.dLdM[2], A.bc);
+        k_adj_seed<real, false><<<gb, kAT, 0, st>>>(fin, hs3, v3<real>(lam, N), gh3, partials, G, A.dLdE, A.dLdM[0],
+                                                    A.dLdM[1], A.dLdM[2]);
     k_adj_seed_finish<<<1, kAT, 0, st>>>(partials, nb, acc, A.dLdE, (double)N);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    // per-block FP64 records of the stage transposes start at zero
-    e = cudaMemsetAsync(partials, 0, sizeof(double) * 5 * (size_t)nb, st);
+    // the per-site FP64 J and D terms start at zero
+    e = cudaMemsetAsync(gjd, 0, sizeof(double) * 2 * (size_t)N, st);
     if (e != cudaSuccess) return e;
 
     const long long total = A.n_end - A.n0;
@@ -636,11 +702,13 @@ cudaError_t adjoint_run(const AdjointRun<real>& A) {
             L.d_interval = kslot;
             L.stream = st;
             if (stored) {
-                for (int j = 1; j <= S; ++j)
-                    for (int c = 0; c < 3; ++c) {
-                        L.st_k[j - 1][c] = stage_k(j, m) + c * N;
+                for (int c = 0; c < 3; ++c) {
+                    for (int j = 1; j <= S; ++j) {
+                        L.st_n[j - 1][c] = stage_sn(j, m) + c * N;
                         if (j >= 2) L.st_x[j - 2][c] = stage_x(j, m) + c * N;
                     }
+                    L.st_y[c] = stage_y(m) + c * N;
+                }
             }
             e = launch_step<real>(L);
             if (e != cudaSuccess) return e;
@@ -650,40 +718,41 @@ cudaError_t adjoint_run(const AdjointRun<real>& A) {
             const long long n = start + m;
             const bool pul = A.noise && (n % A.R) == (A.R / 2);
             const real* s = seg + (size_t)(m - 1) * len;
-            // stages X_j and K_j = dt f(X_j); the first stage's input is s itself
-            const real* Xs[6];
-            real* Kp[6];
-            for (int j = 0; j < S; ++j) Kp[j] = stored ? stage_k(j + 1, m) : Kst[j];
-            for (int j = 0; j < S && stored; ++j) Xs[j] = j == 0 ? s : stage_x(j + 1, m);
+            // stages X_j and K_j = dt f(X_j) (recomputed when not stored); the
+            // first stage's input is s itself
+            StageIn<real> in[6];
+            for (int j = 0; j < S; ++j) {
+                in[j].x = cv3<real>((j == 0) ? s : (stored ? stage_x(j + 1, m) : X[j]), N);
+                in[j].sn = cv3<real>(stored ? stage_sn(j + 1, m) : nullptr, N);
+            }
             for (int j = 0; j < S && !stored; ++j) {
-                if (j == 0) {
-                    Xs[0] = s;
-                } else {
+                if (j > 0) {
                     LinComb<real> lc{};
                     for (int l = 0; l < j; ++l) {
                         lc.K[l] = Kst[l];
                         lc.coef[l] = (real)tb.a[j][l];
                     }
                     launch_lincomb<real>(j, X[j], s, lc, len, st);
-                    Xs[j] = X[j];
                 }
+                const V3<real> K3 = v3<real>(Kst[j], N);
                 if (A.precession) {
-                    if (HS) k_adj_rhs<real, true, true><<<grid_for(N), kAT, 0, st>>>(Xs[j], hs, Kst[j], g.nx, g.ny, g.nz, J, twoD, H0, H1, H2, lamb, dt, A.bc);
-                    else k_adj_rhs<real, true, false><<<grid_for(N), kAT, 0, st>>>(Xs[j], nullptr, Kst[j], g.nx, g.ny, g.nz, J, twoD, H0, H1, H2, lamb, dt, A.bc);
+                    if (HS) k_adj_rhs<real, true, true><<<gb, kAT, 0, st>>>(in[j].x, hs3, K3, G);
+                    else k_adj_rhs<real, true, false><<<gb, kAT, 0, st>>>(in[j].x, hs3, K3, G);
                 } else {
-                    if (HS) k_adj_rhs<real, false, true><<<grid_for(N), kAT, 0, st>>>(Xs[j], hs, Kst[j], g.nx, g.ny, g.nz, J, twoD, H0, H1, H2, lamb, dt, A.bc);
-                    else k_adj_rhs<real, false, false><<<grid_for(N), kAT, 0, st>>>(Xs[j], nullptr, Kst[j], g.nx, g.ny, g.nz, J, twoD, H0, H1, H2, lamb, dt, A.bc);
+                    if (HS) k_adj_rhs<real, false, true><<<gb, kAT, 0, st>>>(in[j].x, hs3, K3, G);
+                    else k_adj_rhs<real, false, false><<<gb, kAT, 0, st>>>(in[j].x, hs3, K3, G);
                 }
             }
             TopArgs<real> ta{};
-            ta.lam = lam;
+            ta.lam = v3<real>(lam, N);
             ta.s = s;
+            ta.ystored = cv3<real>(stored ? stage_y(m) : nullptr, N);
             for (int l = 0; l < S; ++l) {
-                ta.yc.K[l] = Kp[l];
+                ta.yc.K[l] = Kst[l];
                 ta.yc.coef[l] = (real)tb.b[l];
             }
             for (int j = 0; j < S; ++j) {
-                ta.LK[j] = LK[j];
+                ta.LK[j] = v3<real>(LK[j], N);
                 ta.b[j] = (real)tb.b[j];
             }
             ta.renorm = A.renorm;
@@ -692,36 +761,37 @@ cudaError_t adjoint_run(const AdjointRun<real>& A) {
             ta.replica = A.replica;
             ta.k = (n - 1) / A.R;
             ta.sigma = (real)A.sigma;
-            ta.xlast = Xs[S - 1];
-            ta.hs = hs;
-            ta.w = wb[(S - 1) & 1];
-            ta.u = ub[(S - 1) & 1];
-            ta.gh = A.g_h;
-            ta.partials = partials;
-            launch_top_w<real>(A.precession != 0, HS, S, ta, G, nb, st);
+            ta.last = in[S - 1];
+            ta.hs = hs3;
+            ta.w = v3<real>(wb[(S - 1) & 1], N);
+            ta.u = v3<real>(ub[(S - 1) & 1], N);
+            ta.gh = gh3;
+            ta.gjd = gjd;
+            launch_top_w<real>(A.precession != 0, HS, S, ta, G, gb, st);
             for (int j = S - 1; j >= 0; --j) {
                 XWArgs<real> xa{};
-                xa.w = wb[j & 1];
-                xa.u = ub[j & 1];
-                xa.lam = lam;
+                xa.w = cv3<real>(wb[j & 1], N);
+                xa.u = cv3<real>(ub[j & 1], N);
+                xa.lam = v3<real>(lam, N);
                 for (int l = 0; l < j; ++l) {
-                    xa.LK[l] = LK[l];
+                    xa.LK[l] = v3<real>(LK[l], N);
                     xa.a[l] = (real)tb.a[j][l];
                 }
                 if (j > 0) {
-                    xa.xprev = Xs[j - 1];
-                    xa.wn = wb[(j - 1) & 1];
-                    xa.un = ub[(j - 1) & 1];
+                    xa.prev = in[j - 1];
+                    xa.wn = v3<real>(wb[(j - 1) & 1], N);
+                    xa.un = v3<real>(ub[(j - 1) & 1], N);
                 }
-                xa.hs = hs;
-                xa.gh = A.g_h;
-                xa.partials = partials;
-                launch_xw<real>(A.precession != 0, HS, j, xa, G, nb, st);
+                xa.hs = hs3;
+                xa.gh = gh3;
+                xa.gjd = gjd;
+                launch_xw<real>(A.precession != 0, HS, j, xa, G, gb, st);
             }
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
     }
-    k_adj_accumulate<<<1, kAT, 0, st>>>(partials, nb, acc, 1.0);
+    k_adj_sum_jd<<<2, kAT, 0, st>>>(gjd, N, acc);
+    k_adj_sum_gh<<<3, kAT, 0, st>>>(gh, N, acc);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // results: gradient accumulators to the host, dL/ds_0 to the caller
     if (A.g_s0) {

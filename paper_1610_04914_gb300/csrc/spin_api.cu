@@ -387,7 +387,26 @@ int spin_step_pulse(spin_lattice* h, int64_t nsteps) {
     const int R = h->p.steps_per_pulse;
     while (nsteps > 0) {
         if (h->rec_active) {
-            // recording: single eager steps so every checkpoint step is seen
+            // recording: a whole noise interval is replayed from the graph when
+            // no checkpoint falls strictly inside it (one at its end is taken
+            // after the replay); otherwise single eager steps, so that every
+            // checkpoint step is seen
+            const long long d0 = h->n - h->rec_n0;
+            const long long next_ckpt = (d0 / h->rec_K + 1) * h->rec_K;
+            if (h->n % R == 0 && nsteps >= R && h->eager_intervals > 0 && d0 >= 0 && next_ckpt >= d0 + R) {
+                if (!h->graph[h->cur]) {
+                    int rc = capture_interval(h, h->cur);
+                    if (rc != SPIN_OK) return rc;
+                }
+                SPIN_CUDA(h, cudaGraphLaunch(h->graph[h->cur], h->st));
+                h->n += R;
+                if (R & 1) h->cur ^= 1;
+                nsteps -= R;
+                int rc = record_if_due(h);
+                if (rc != SPIN_OK) return rc;
+                continue;
+            }
+            if (h->n % R == 0 && nsteps >= R) h->eager_intervals++;
             SPIN_CUDA(h, launch_one_step(h, h->cur, h->n + 1, h->st));
             h->cur ^= 1;
             h->n += 1;

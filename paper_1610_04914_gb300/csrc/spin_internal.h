@@ -51,11 +51,13 @@ struct StepLaunch {
     cudaStream_t stream;
     int force_generic;
     int bc;                // 0 periodic, 1 free boundaries
-    // FP32 fused path only: if st_k[0][0] is set, the step also writes the
-    // stage inputs X_j (j = 2..S, st_x[j-2]) and increments K_j = dt f(X_j)
-    // (j = 1..S, st_k[j-1]) of every site, component arrays of 3 x N
+    // FP32 fused path only: if st_n[0][0] is set, the step also writes, at
+    // every site, the stage inputs X_j (j = 2..S, st_x[j-2]), the neighbour
+    // sums sum_nn X_j of every stage (j = 1..S, st_n[j-1]) and the
+    // unnormalised RK result y (st_y), component arrays of 3 x N
     real* st_x[3][3];
-    real* st_k[4][3];
+    real* st_n[4][3];
+    real* st_y[3];
 };
 
 template <typename real>

@@ -70,11 +70,12 @@ struct PatchArgs {
     int pair8;         // 1: each thread's column pair is one aligned 8-byte word of every input plane
     int pair8out;      // 1: the same for the output planes
     // stage store (STORE variant, for the adjoint's recomputation): at the
-    // output sites, the stage inputs X_j (j = 2..S, stx[j-2]) and the stage
-    // increments K_j = dt f(X_j) (j = 1..S, stk[j-1]), component arrays in the
-    // lattice's layout
+    // output sites, the stage inputs X_j (j = 2..S, stx[j-2]), the stage
+    // neighbour sums sum_nn X_j (j = 1..S, stn[j-1]) and the unnormalised RK
+    // result y (sty), component arrays in the lattice's layout
     float* stx[3][3];
-    float* stk[4][3];
+    float* stn[4][3];
+    float* sty[3];
     float dt;
     int* err;          // device status word for bounded waits (nullable; no wait in this kernel sets it)
 };
@@ -326,19 +327,30 @@ __device__ __forceinline__ void patch_iteration(const PatchArgs& a, PRings<S, HS
                     f[2] = mul2(sp2(-a.lambda), bz);
                 }
                 if (STORE) {
-                    // stage input and increment of plane t+S-j at the output sites
+                    // stage input and neighbour sum of plane t+S-j at the output sites
                     const int pz = t + S - j;
                     if (pz >= z0 && pz < z0 + a.tz && pz < a.nz) {
                         const int base = pz * th.plane;
+                        if (a.pair8out) {
+                            // both columns of the pair are outputs or neither: 8-byte stores
+                            if (th.out[rr][0]) {
+                                const int site = base + th.col[rr][0];
 #pragma unroll
-                        for (int e = 0; e < 2; ++e) {
-                            if (!th.out[rr][e]) continue;
-                            const int site = base + th.col[rr][e];
+                                for (int c = 0; c < 3; ++c) {
+                                    *reinterpret_cast<f2*>(a.stn[j - 1][c] + site) = sum[rr][c];
+                                    if (j >= 2) *reinterpret_cast<f2*>(a.stx[j >= 2 ? j - 2 : 0][c] + site) = cen[rr][c];
+                                }
+                            }
+                        } else {
 #pragma unroll
-                            for (int c = 0; c < 3; ++c) {
-                                const f2 kk = mul2(sp2(a.dt), f[c]);
-                                a.stk[j - 1][c][site] = e == 0 ? kk.x : kk.y;
-                                if (j >= 2) a.stx[j >= 2 ? j - 2 : 0][c][site] = e == 0 ? cen[rr][c].x : cen[rr][c].y;
+                            for (int e = 0; e < 2; ++e) {
+                                if (!th.out[rr][e]) continue;
+                                const int site = base + th.col[rr][e];
+#pragma unroll
+                                for (int c = 0; c < 3; ++c) {
+                                    a.stn[j - 1][c][site] = e == 0 ? sum[rr][c].x : sum[rr][c].y;
+                                    if (j >= 2) a.stx[j >= 2 ? j - 2 : 0][c][site] = e == 0 ? cen[rr][c].x : cen[rr][c].y;
+                                }
                             }
                         }
                     }
@@ -359,6 +371,17 @@ __device__ __forceinline__ void patch_iteration(const PatchArgs& a, PRings<S, HS
 #pragma unroll
             for (int rr = 0; rr < PY; ++rr) {
                 f2 ox = r.y[slot][rr][0], oy = r.y[slot][rr][1], oz = r.y[slot][rr][2];
+                if (STORE) {
+                    // the unnormalised RK result, for the adjoint's renormalisation transpose
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        if (!th.out[rr][e]) continue;
+                        const int site = base + th.col[rr][e];
+                        a.sty[0][site] = e == 0 ? ox.x : ox.y;
+                        a.sty[1][site] = e == 0 ? oy.x : oy.y;
+                        a.sty[2][site] = e == 0 ? oz.x : oz.y;
+                    }
+                }
                 if (a.renorm) {
                     const f2 n2 = fma2(ox, ox, fma2(oy, oy, mul2(oz, oz)));
                     const f2 inv = make_float2(rsqrtf(n2.x), rsqrtf(n2.y));
@@ -754,12 +777,14 @@ cudaError_t launch_step_patch(const StepLaunch<float>& L) {
     const bool hs = L.hs[0] != nullptr;
     const bool prec = L.precession != 0;
     cudaError_t e;
-    if (L.st_k[0][0]) {
-        for (int j = 0; j < S; ++j)
-            for (int c = 0; c < 3; ++c) {
-                a.stk[j][c] = L.st_k[j][c];
+    if (L.st_n[0][0]) {
+        for (int c = 0; c < 3; ++c) {
+            for (int j = 0; j < S; ++j) {
+                a.stn[j][c] = L.st_n[j][c];
                 if (j + 1 < S) a.stx[j][c] = L.st_x[j][c];
             }
+            a.sty[c] = L.st_y[c];
+        }
         a.dt = (float)L.dt;
         e = S == 4 ? patch_store_dispatch<4>(a, grid, L.stream, prec, hs, false)
                    : patch_store_dispatch<2>(a, grid, L.stream, prec, hs, false);

@@ -74,9 +74,10 @@ def test_generic_path_needs_more_workspace():
 
 
 def test_backward_workspace_holds_the_stage_store_when_it_applies(lib):
-    """The adjoint keeps a checkpoint segment's stage inputs and increments
-    ((2 x stages - 1) x K arrays of 3N) only for FP32 chain tableaus on the
-    fused path and while they take at most 8 GiB (host logic, no device)."""
+    """The adjoint keeps a checkpoint segment's stage inputs, stage neighbour
+    sums and unnormalised RK results (2 x stages x K arrays of 3N) only for
+    FP32 chain tableaus on the fused path and while they take at most 8 GiB
+    (host logic, no device)."""
     import paper_1610_04914_gb300 as sp
 
     def ws(**kw):
@@ -87,10 +88,10 @@ def test_backward_workspace_holds_the_stage_store_when_it_applies(lib):
     arr = lambda n, elt: (3 * n * elt + 255) // 256 * 256
     n64 = 64 ** 3
     base32 = ws(path=1)                          # per-stage forward path: no stage store
-    assert ws() - base32 == 7 * 50 * arr(n64, 4)
-    assert ws(K=10) - ws(K=10, path=1) == 7 * 10 * arr(n64, 4)
-    assert ws(integrator=sp.RK2_MIDPOINT) - ws(integrator=sp.RK2_MIDPOINT, path=1) == 3 * 50 * arr(n64, 4)
+    assert ws() - base32 == 8 * 50 * arr(n64, 4)
+    assert ws(K=10) - ws(K=10, path=1) == 8 * 10 * arr(n64, 4)
+    assert ws(integrator=sp.RK2_MIDPOINT) - ws(integrator=sp.RK2_MIDPOINT, path=1) == 4 * 50 * arr(n64, 4)
     assert ws(precision=64) == ws(precision=64, path=1)                     # FP64: stages recomputed
     assert ws(integrator=sp.RK5_BUTCHER) == ws(integrator=sp.RK5_BUTCHER, path=1)   # not a chain tableau
-    big = dict(nx=256, ny=256, nz=256)                # 7 x 50 x 201 MB > 8 GiB
+    big = dict(nx=256, ny=256, nz=256)                # 8 x 50 x 201 MB > 8 GiB
     assert ws(**big) == ws(**big, path=1)
