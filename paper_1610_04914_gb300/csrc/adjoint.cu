@@ -45,20 +45,6 @@ namespace {
 constexpr int kAT = 256;                 // threads per block (8 warps)
 constexpr int kAW = kAT / 32;
 
-// Exact float -> double: sign, exponent rebased from 127 to 1023, mantissa
-// shifted into the top of the 52-bit field.  Zeros keep their sign; only
-// subnormal, infinite and NaN floats take the hardware conversion.
-__device__ __forceinline__ double to_f64(float f) {
-    const unsigned b = __float_as_uint(f);
-    const unsigned e = (b >> 23) & 0xFFu;
-    const unsigned long long sign = (unsigned long long)(b & 0x80000000u) << 32;
-    if ((b & 0x7FFFFFFFu) == 0u) return __longlong_as_double((long long)sign);
-    if (e == 0u || e == 0xFFu) return (double)f;
-    return __longlong_as_double(
-        (long long)(sign | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(b & 0x7FFFFFu) << 29)));
-}
-__device__ __forceinline__ double to_f64(double d) { return d; }
-
 // A site of the lattice with its six neighbours (x-1, x+1, y-1, y+1, z-1, z+1;
 // periodic wrap) and their weights (0 across a face of a free-boundary
 // lattice).  All indices fit in 32 bits (N < 2^31).

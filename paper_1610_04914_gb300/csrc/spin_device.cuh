@@ -147,6 +147,23 @@ __device__ __forceinline__ void pulse_site(real& sx, real& sy, real& sz, uint64_
     pulse_rotate<real>(sx, sy, sz, sigma * g0, sigma * g1, sigma * g2);
 }
 
+// Exact float -> double for FP64 accumulation of FP32 terms: sign, exponent
+// rebased from 127 to 1023, mantissa shifted into the top of the 52-bit field
+// -- integer operations only, because this GPU's FP64 pipe, which the
+// hardware conversion uses, runs at ~1/76 of the FP32 rate and is needed for
+// the FP64 additions themselves.  Zeros keep their sign; subnormal, infinite
+// and NaN floats take the hardware conversion.
+__device__ __forceinline__ double to_f64(float f) {
+    const unsigned b = __float_as_uint(f);
+    const unsigned e = (b >> 23) & 0xFFu;
+    const unsigned long long sign = (unsigned long long)(b & 0x80000000u) << 32;
+    if ((b & 0x7FFFFFFFu) == 0u) return __longlong_as_double((long long)sign);
+    if (e == 0u || e == 0xFFu) return (double)f;
+    return __longlong_as_double(
+        (long long)(sign | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(b & 0x7FFFFFu) << 29)));
+}
+__device__ __forceinline__ double to_f64(double d) { return d; }
+
 // Right-hand side of Eq. (LLL) with a rectangular-noise field zeta, which
 // enters the precession term only:  f = s x (H + zeta) - lambda s x (s x H).
 template <typename real>

@@ -153,11 +153,15 @@ def test_fp32_trajectory_16cubed(gpu, orc):
 @pytest.mark.parametrize("shape", [(16, 16, 16), (5, 7, 3), (1, 1, 1), (2, 2, 2), (130, 64, 96)])
 def test_observables(gpu, orc, prec, shape):
     """M and E against the oracle on the same values.  FP64 states: FP64
-    arithmetic throughout (1e-13).  FP32 states: per-site terms in FP32 (a bond
-    sum of three products of float spins carries at most a few 1e-7 relative
-    error, the per-site energy |e_i| < 7 here), accumulated in FP64 per row:
-    bounds 1e-6 for M and 5e-6 for E.  (130, 64, 96): rows of 130 sites, five
-    columns per lane of which the last is ragged."""
+    arithmetic throughout (1e-13).  FP32 states: each lane pre-sums its
+    k = ceil(nx/32) sites of a row in FP32 (the spin components exactly as
+    stored, and each site's energy term formed in FP32 like the stencil), and
+    everything longer is summed in FP64.  M: a pre-sum of k values of size <= 1
+    carries at most (k-1) k 2^-24 absolute error, so M per spin is off by at
+    most (k-1) 2^-24 <= 2.4e-7 for rows up to 160 sites: bound 1e-6.  E: each
+    site's term (|e_i| < 7 here, ~8 roundings) is off by at most 3.3e-6 and the
+    pre-sums add (k-1) k 7 2^-24 / k per site: bound 5e-6.  (130, 64, 96):
+    rows of 130 sites, five sites per lane of which the last is ragged."""
     nx, ny, nz = shape
     p = gpu.Params(nx, ny, nz, J=0.8, D=0.3, H=(0.1, -0.2, 0.3), precision=prec)
     s0 = spin_inputs.random_spins(nx, ny, nz, seed=9)
