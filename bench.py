@@ -448,26 +448,42 @@ def batch_timing(sp, torch, dev, flush, stream, hbm_peak, intervals=3):
     p = sp.Params(1, 1, 1, J=w["J"], D=w["D"], H=w["H"], lam=w["lam"], dt=w["dt"], R=w["R"], seed=w["seed"],
                   precision=32)
     states = [spin_inputs.random_spins(int(l), int(l), int(l), seed=1000 + r) for r, l in enumerate(L)]
+    def run_intervals(b):
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                b.step(p.R)
+            evs = []
+            for _ in range(intervals):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                b.step(p.R)
+                e1.record(stream)
+                evs.append((e0, e1))
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(c) for a, c in evs) / 1e3
+
     with torch.cuda.stream(stream):
-        b = sp.Batch(p, L, T, states, device=dev, stream=stream)
-        ntot = int(b.offsets[-1])
-        for _ in range(3):
-            b.step(p.R)
-        evs = []
-        for _ in range(intervals):
-            flush.zero_()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            b.step(p.R)
-            e1.record(stream)
-            evs.append((e0, e1))
-    torch.cuda.synchronize()
-    t = sum(a.elapsed_time(c) for a, c in evs) / 1e3
+        # tiling autotuned per size class at create (fresh, not from a cache)
+        b = sp.Batch(p, L, T, states, device=dev, stream=stream, use_cache=False)
+    ntot = int(b.offsets[-1])
+    tuned = b.tiling()
+    items_tuned = b.nitems
+    t = run_intervals(b)
+    rows = sp.spin_batch_tile_rows(p.integrator)
+    with torch.cuda.stream(stream):
+        b.set_tiling({l: (rows[0], 32) for l in tuned})
+    t_default = run_intervals(b)
+    items_default = b.nitems
     rate = ntot * p.R * intervals / t
     b.close()
     out = {"workload": "512 replicas, L in {16,24,32,48,64}, T in [0.2,2], FP32 RK4 dt=0.2, pulse every 10",
            "spins": ntot, "value": rate, "unit": "spin-steps/s", "ms_per_interval": 1e3 * t / intervals,
-           "chunk_planes": b.chunk_planes, "work_items": b.nitems,
+           "tiling": {str(l): {"tile_rows": r, "chunk": k} for l, (r, k) in sorted(tuned.items())},
+           "work_items": items_tuned,
+           "default_tiling": {"tile_rows": rows[0], "chunk": 32, "work_items": items_default,
+                              "ms_per_interval": 1e3 * t_default / intervals},
+           "tuned_speedup_vs_default": t_default / t,
            "hbm_frac_algorithmic": BYTES_PER_SPIN_STEP_FP32 * rate / 1e9 / hbm_peak}
     # comparison arms: the same replicas as separate plain lattices, one
     # interval each, stepped back to back on the stream (FP32: what batching

@@ -242,10 +242,23 @@ int spin_noise_draw(uint64_t seed, int64_t k, int64_t replica, int64_t n_sites,
  * State: three caller-owned device float arrays (s_x, s_y, s_z) holding the
  * replicas back to back, replica r at offset offsets[r] (spin_batch_offsets:
  * offsets[r] = sum_{q<r} L[q]^3, offsets[nrep] = total), each replica x
- * fastest.  chunk_planes: z-chunk length of the work items; 0 lets the library
- * time the candidates 8, 16, 32, 64 on the real tables at create (a short
- * synchronous autotune, cached per process by the multiset of sizes) and keep
- * the fastest; spin_batch_tuning reports the choice.
+ * fastest.
+ * Tiling: chosen per size class (the replicas sharing one side L) as a CTA
+ * tile height tile_rows (spin_batch_tile_rows lists the heights offered for
+ * an integrator; a tile writes tile_rows - 2 x stages rows, the rest is the
+ * stage halo) and a z-chunk length chunk (planes per work item, >= 1).  It
+ * changes the schedule only: every tiling gives bit-identical states.
+ * chunk_planes at create: > 0 gives every class that chunk and the tallest
+ * tile; -1 gives every class the default (tallest tile, chunk 32) without
+ * timing; 0 autotunes: per class, in decreasing order of spins, each tile
+ * height x chunk in {8, 16, 32, 64} is timed on the whole batch (one step,
+ * input buffer to scratch, state untouched; synchronous) with the other
+ * classes held, and the fastest kept.  Classes tuned earlier in the process
+ * for the same (L, precision, integrator) reuse that choice.
+ * spin_batch_tiling reports the per-class choice; spin_batch_set_tiling pins
+ * the listed classes (SPIN_EINVAL for a side no replica has, a height not
+ * offered, or chunk < 1); spin_batch_autotune tunes the classes not pinned.
+ * Both synchronise the stream and rebuild the work-item table.
  * Samples: after steps with n mod R == 0 a record of nrep x 5 doubles
  * (n, M_x, M_y, M_z, E per replica) goes to a ring of
  * SPIN_BATCH_SAMPLE_RING records.
@@ -258,7 +271,16 @@ int spin_batch_workspace_size(const spin_params* p, int32_t nrep, const int32_t*
 int spin_batch_create(const spin_params* p, int32_t nrep, const int32_t* L, const double* T, void* sx,
                       void* sy, void* sz, int32_t chunk_planes, void* workspace, size_t workspace_bytes,
                       void* cuda_stream, spin_batch** out);
+/* chunk of the class holding the most spins, and the number of work items */
 int spin_batch_tuning(const spin_batch* b, int32_t* chunk_planes, int32_t* nitems);
+/* tile heights offered for integrator (the tallest first) into rows[max]; *n = their count */
+int spin_batch_tile_rows(int32_t integrator, int32_t max, int32_t* rows, int32_t* n);
+/* per size class (first-appearance order): side, tile height, chunk into arrays of max entries; *n = classes */
+int spin_batch_tiling(const spin_batch* b, int32_t max, int32_t* L, int32_t* tile_rows, int32_t* chunk,
+                      int32_t* n);
+int spin_batch_set_tiling(spin_batch* b, int32_t n, const int32_t* L, const int32_t* tile_rows,
+                          const int32_t* chunk);
+int spin_batch_autotune(spin_batch* b);
 int spin_batch_step_pulse(spin_batch* b, int64_t nsteps);
 /* current M_x, M_y, M_z, E, non-finite count per replica into host out[5*nrep]; synchronises */
 int spin_batch_observables(spin_batch* b, double* out);

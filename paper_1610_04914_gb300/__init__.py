@@ -14,4 +14,4 @@ from .lattice import (EscapeReplicas, Lattice, Params, SingleSpins, SpinRunFn, s
                       spin_lattice_destroy, spin_metropolis_color, spin_metropolis_sweeps, spin_noise_draw, spin_observables,
                       spin_observables_noalloc, spin_samples,
                       spin_set_step, spin_step_pulse, spin_workspace_size)
-from .batch import Batch, spin_batch_offsets, spin_batch_workspace_size  # noqa: F401,E402
+from .batch import Batch, spin_batch_offsets, spin_batch_tile_rows, spin_batch_workspace_size  # noqa: F401,E402

@@ -53,6 +53,7 @@ EXPORTS = [
     "spin_last_error", "spin_noise_draw", "spin_observables_noalloc", "spin_record_store_size",
     "spin_record_begin", "spin_record_end", "spin_backward_workspace_size", "spin_backward",
     "spin_batch_offsets", "spin_batch_workspace_size", "spin_batch_create", "spin_batch_tuning",
+    "spin_batch_tile_rows", "spin_batch_tiling", "spin_batch_set_tiling", "spin_batch_autotune",
     "spin_batch_step_pulse", "spin_batch_observables", "spin_batch_samples", "spin_batch_destroy",
     "spin_batch_last_error", "spin_single_prepare", "spin_single_run", "spin_single_escape", "spin_metropolis_sweeps", "spin_metropolis_color",
 ]
@@ -95,6 +96,10 @@ def load(path: str = LIB_PATH):
     L.spin_batch_workspace_size.argtypes = [P(spin_params), i32, P(i32), P(sz)]
     L.spin_batch_create.argtypes = [P(spin_params), i32, P(i32), P(d), vp, vp, vp, i32, vp, sz, vp, P(vp)]
     L.spin_batch_tuning.argtypes = [vp, P(i32), P(i32)]
+    L.spin_batch_tile_rows.argtypes = [i32, i32, P(i32), P(i32)]
+    L.spin_batch_tiling.argtypes = [vp, i32, P(i32), P(i32), P(i32), P(i32)]
+    L.spin_batch_set_tiling.argtypes = [vp, i32, P(i32), P(i32), P(i32)]
+    L.spin_batch_autotune.argtypes = [vp]
     L.spin_batch_step_pulse.argtypes = [vp, i64]
     L.spin_batch_observables.argtypes = [vp, P(d)]
     L.spin_batch_samples.argtypes = [vp, P(d), i64, P(i64)]

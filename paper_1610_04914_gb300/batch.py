@@ -1,6 +1,7 @@
 """Batched replicas through the C-ABI (spin_batch_*): argument marshalling, a
-JSON cache of the library's z-chunk autotuning, and per-replica views of the
-concatenated state."""
+JSON cache of the library's per-size-class tiling choice (tile height and
+z-chunk, keyed by side L, precision and integrator), and per-replica views of
+the concatenated state."""
 from __future__ import annotations
 
 import ctypes
@@ -14,14 +15,25 @@ from . import _binding as B
 from ._binding import check
 from .lattice import Params, _stream_ptr
 
+DEFAULT_TILING = -1   # chunk_planes value: every class on the default tiling, no timing
+
 
 def _cache_path() -> str:
     base = os.environ.get("XDG_CACHE_HOME") or os.path.join(os.path.expanduser("~"), ".cache")
-    return os.path.join(base, "spinpulse", "batch_tuning.json")
+    return os.path.join(base, "spinpulse", "batch_tiling.json")
 
 
-def _tune_key(p: Params, L) -> str:
-    return f"p{p.precision}-i{p.integrator}-L" + ",".join(str(v) for v in sorted(int(x) for x in L))
+def _class_key(p: Params, L: int) -> str:
+    return f"p{p.precision}-i{p.integrator}-L{int(L)}"
+
+
+def _load_cache() -> dict:
+    try:
+        with open(_cache_path()) as f:
+            c = json.load(f)
+        return c if isinstance(c, dict) else {}
+    except (OSError, ValueError):
+        return {}
 
 
 def spin_batch_offsets(L) -> np.ndarray:
@@ -40,14 +52,27 @@ def spin_batch_workspace_size(p: Params, L) -> int:
     return int(out.value)
 
 
+def spin_batch_tile_rows(integrator: int) -> list:
+    """CTA tile heights the batched step offers for an integrator, tallest first."""
+    rows = (ctypes.c_int32 * 8)()
+    n = ctypes.c_int32()
+    check(B.load().spin_batch_tile_rows(int(integrator), 8, rows, ctypes.byref(n)))
+    return list(rows[:n.value])
+
+
 class Batch:
     """nrep cubic periodic replicas of sides L[r] and temperatures T[r].
 
     ``states``: list of (3, L, L, L) arrays (or one (3, total) array in the
-    concatenated layout).  ``chunk_planes``: None = use the cached tuning or let
-    the library autotune at create; an int forces the z-chunk length."""
+    concatenated layout).  Tiling (schedule only; the states are bit-identical
+    under every choice): ``tiling`` = {L: (tile_rows, chunk)} pins those size
+    classes; ``chunk_planes`` = int gives every class that z-chunk on the
+    default tile height (``DEFAULT_TILING`` = the library default, untimed);
+    otherwise classes found in the JSON cache take the cached choice and the
+    library autotunes the rest at create (then cached, when ``use_cache``)."""
 
-    def __init__(self, p: Params, L, T, states, chunk_planes=None, device="cuda", stream=None, use_cache=True):
+    def __init__(self, p: Params, L, T, states, chunk_planes=None, tiling=None, device="cuda", stream=None,
+                 use_cache=True):
         self.p = p
         self.L = [int(v) for v in L]
         self.T = [float(v) for v in T]
@@ -61,14 +86,14 @@ class Batch:
         self.state = torch.from_numpy(np.ascontiguousarray(flat)).to(device)
         nbytes = spin_batch_workspace_size(p, self.L)
         self.workspace = torch.empty(nbytes // 8 + 32, dtype=torch.float64, device=device)
-        key = _tune_key(p, self.L)
-        cache = {}
-        if chunk_planes is None and use_cache and os.path.exists(_cache_path()):
-            try:
-                cache = json.load(open(_cache_path()))
-            except Exception:
-                cache = {}
-        hint = int(chunk_planes) if chunk_planes is not None else int(cache.get(key, 0))
+        pinned = {int(k): (int(v[0]), int(v[1])) for k, v in (tiling or {}).items()}
+        cache = _load_cache() if (use_cache and chunk_planes is None) else {}
+        if chunk_planes is None:
+            for l in sorted(set(self.L)):
+                hit = cache.get(_class_key(p, l))
+                if l not in pinned and isinstance(hit, list) and len(hit) == 2:
+                    pinned[l] = (int(hit[0]), int(hit[1]))
+        hint = int(chunk_planes) if chunk_planes is not None else DEFAULT_TILING
         Lc = (ctypes.c_int32 * self.nrep)(*self.L)
         Tc = (ctypes.c_double * self.nrep)(*self.T)
         h = ctypes.c_void_p()
@@ -77,16 +102,48 @@ class Batch:
                                          self.workspace.data_ptr(), self.workspace.numel() * 8,
                                          _stream_ptr(stream), ctypes.byref(h)))
         self.handle = h
+        if pinned:
+            self.set_tiling(pinned)
+        if chunk_planes is None:
+            tuned = set(self.L) - set(pinned)
+            if tuned:
+                self._check(B.load().spin_batch_autotune(self.handle))
+                if use_cache:
+                    now = self.tiling()
+                    cache = _load_cache()
+                    for l in tuned:
+                        cache[_class_key(p, l)] = list(now[l])
+                    try:
+                        os.makedirs(os.path.dirname(_cache_path()), exist_ok=True)
+                        with open(_cache_path(), "w") as f:
+                            json.dump(cache, f, indent=0, sort_keys=True)
+                    except OSError:
+                        pass
+        self._refresh()
+
+    def _refresh(self):
         cp, ni = ctypes.c_int32(), ctypes.c_int32()
-        check(B.load().spin_batch_tuning(h, ctypes.byref(cp), ctypes.byref(ni)))
+        check(B.load().spin_batch_tuning(self.handle, ctypes.byref(cp), ctypes.byref(ni)))
         self.chunk_planes, self.nitems = cp.value, ni.value
-        if chunk_planes is None and use_cache and key not in cache:
-            try:
-                os.makedirs(os.path.dirname(_cache_path()), exist_ok=True)
-                cache[key] = self.chunk_planes
-                json.dump(cache, open(_cache_path(), "w"))
-            except OSError:
-                pass
+
+    def tiling(self) -> dict:
+        """{L: (tile_rows, chunk)} per size class."""
+        m = len(set(self.L))
+        Ls, rows, ch = (ctypes.c_int32 * m)(), (ctypes.c_int32 * m)(), (ctypes.c_int32 * m)()
+        n = ctypes.c_int32()
+        self._check(B.load().spin_batch_tiling(self.handle, m, Ls, rows, ch, ctypes.byref(n)))
+        return {int(Ls[i]): (int(rows[i]), int(ch[i])) for i in range(n.value)}
+
+    def set_tiling(self, tiling: dict) -> "Batch":
+        """Pin {L: (tile_rows, chunk)}; the other classes keep theirs."""
+        n = len(tiling)
+        ks = list(tiling)
+        Ls = (ctypes.c_int32 * n)(*[int(k) for k in ks])
+        rows = (ctypes.c_int32 * n)(*[int(tiling[k][0]) for k in ks])
+        ch = (ctypes.c_int32 * n)(*[int(tiling[k][1]) for k in ks])
+        self._check(B.load().spin_batch_set_tiling(self.handle, n, Ls, rows, ch))
+        self._refresh()
+        return self
 
     def _check(self, rc):
         if rc < 0:

@@ -38,7 +38,10 @@ struct spin_batch {
     BatchRep* reps;
     BatchItem* items;
     int nitems;
-    int chunk_planes;      // chosen z-chunk target
+    // tiling per size class (all replicas of one side L): CTA tile variant,
+    // z-chunk target, and whether the caller pinned it (autotune skips those)
+    std::vector<int> cls_L, cls_var, cls_chunk, cls_pinned;
+    std::vector<int> var_first;   // items of tile variant v: [var_first[v], var_first[v+1])
     ObsBlock* oblocks;
     int* first_block;
     int nblocks_obs;
@@ -62,6 +65,7 @@ constexpr size_t kAlign = 256;
 size_t al(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 constexpr int kRowsPerObsBlock = 256;
 const int kChunkCandidates[] = {8, 16, 32, 64};
+constexpr int kDefaultChunk = 32;
 
 int bset_err(spin_batch* b, int code, const char* fmt, ...) {
     if (b) {
@@ -96,35 +100,57 @@ int validate_batch(const spin_params* p, int nrep, const int32_t* L, const doubl
     return SPIN_OK;
 }
 
-std::vector<BatchItem> make_items(const spin_params* p, int nrep, const int32_t* L, int chunk_planes,
-                                  std::vector<int>* tz_out) {
+// Work items of every replica under its class's tiling, grouped by tile
+// variant (one launch each); within a variant the most expensive items come
+// first, so the block scheduler balances the tail.
+std::vector<BatchItem> make_items(const spin_params* p, int nrep, const int32_t* L, const std::vector<int>& var_of,
+                                  const std::vector<int>& chunk_of, std::vector<int>* tz_out,
+                                  std::vector<int>* var_first) {
     const int S = tableau_for(p->integrator).stages;
-    const int ox = patch_out_x(S), oy = patch_out_y(S);
-    std::vector<std::pair<int, BatchItem>> v;
-    tz_out->assign(nrep, 1);
-    for (int r = 0; r < nrep; ++r) {
-        const int chunks = std::max(1, (L[r] + chunk_planes - 1) / chunk_planes);
-        const int tz = (L[r] + chunks - 1) / chunks;
-        (*tz_out)[r] = tz;
-        const int tx = (L[r] + ox - 1) / ox, ty = (L[r] + oy - 1) / oy;
-        const int used = (L[r] + tz - 1) / tz;
-        for (int bz = 0; bz < used; ++bz)
-            for (int by = 0; by < ty; ++by)
-                for (int bx = 0; bx < tx; ++bx) v.push_back({tz + 2 * S - 2, BatchItem{r, (short)bx, (short)by, bz}});
-    }
-    // most expensive items first: the block scheduler then balances the tail
-    std::stable_sort(v.begin(), v.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+    const int nv = patch_variants();
+    const int ox = patch_out_x(S);
     std::vector<BatchItem> items;
-    items.reserve(v.size());
-    for (auto& e : v) items.push_back(e.second);
+    tz_out->assign(nrep, 1);
+    var_first->assign(nv + 1, 0);
+    for (int v = 0; v < nv; ++v) {
+        (*var_first)[v] = (int)items.size();
+        const int oy = patch_out_y(S, v);
+        std::vector<std::pair<int, BatchItem>> w;
+        for (int r = 0; r < nrep; ++r) {
+            if (var_of[r] != v) continue;
+            const int chunks = std::max(1, (L[r] + chunk_of[r] - 1) / chunk_of[r]);
+            const int tz = (L[r] + chunks - 1) / chunks;
+            (*tz_out)[r] = tz;
+            const int tx = (L[r] + ox - 1) / ox, ty = (L[r] + oy - 1) / oy;
+            const int used = (L[r] + tz - 1) / tz;
+            for (int bz = 0; bz < used; ++bz)
+                for (int by = 0; by < ty; ++by)
+                    for (int bx = 0; bx < tx; ++bx)
+                        w.push_back({tz + 2 * S - 2, BatchItem{r, (short)bx, (short)by, bz}});
+        }
+        std::stable_sort(w.begin(), w.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+        for (auto& e : w) items.push_back(e.second);
+    }
+    (*var_first)[nv] = (int)items.size();
     return items;
 }
 
+// Largest item table any tiling can produce: per replica, the most items
+// over tile variants and z-chunks of at least the smallest candidate.
 int max_items(const spin_params* p, int nrep, const int32_t* L) {
-    size_t m = 0;
-    std::vector<int> tz;
-    for (int c : kChunkCandidates) m = std::max(m, make_items(p, nrep, L, c, &tz).size());
-    return (int)m;
+    const int S = tableau_for(p->integrator).stages;
+    const int ox = patch_out_x(S);
+    long long m = 0;
+    for (int r = 0; r < nrep; ++r) {
+        long long best = 0;
+        for (int v = 0; v < patch_variants(); ++v) {
+            const int oy = patch_out_y(S, v);
+            const long long t = (long long)((L[r] + ox - 1) / ox) * ((L[r] + oy - 1) / oy) * L[r];
+            best = std::max(best, t);
+        }
+        m += best;
+    }
+    return (int)std::min<long long>(m, 1LL << 30);
 }
 
 int obs_blocks(int nrep, const int32_t* L, std::vector<ObsBlock>* blocks, std::vector<int>* first) {
@@ -220,12 +246,23 @@ cudaError_t batch_observe(spin_batch* b, int buf, bool sample, cudaStream_t st) 
                                     b->d_interval, b->d_sample_count, b->p.steps_per_pulse, st);
 }
 
+// One launch per tile variant in use, each over its slice of the item table.
+cudaError_t batch_step_kernels(spin_batch* b, const StepLaunch<float>& Ls) {
+    for (int v = 0; v < patch_variants(); ++v) {
+        const int n = b->var_first[v + 1] - b->var_first[v];
+        if (n == 0) continue;
+        cudaError_t e = launch_step_patch_batch(Ls, b->items + b->var_first[v], n, b->reps, v);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t batch_one_step(spin_batch* b, int from, long long n_next, cudaStream_t st) {
     const int R = b->p.steps_per_pulse;
     const bool pulse = b->p.noise && (n_next % R) == (R / 2);
     // the step kernel without its epilogue rotation, then the pulse over all
     // sites (every thread busy; same arithmetic as the single-lattice path)
-    cudaError_t e = launch_step_patch_batch(batch_launch_args(b, from, false, st), b->items, b->nitems, b->reps);
+    cudaError_t e = batch_step_kernels(b, batch_launch_args(b, from, false, st));
     if (e != cudaSuccess) return e;
     if (pulse) {
         float* s[3] = {(float*)b->buf[from ^ 1][0], (float*)b->buf[from ^ 1][1], (float*)b->buf[from ^ 1][2]};
@@ -236,12 +273,31 @@ cudaError_t batch_one_step(spin_batch* b, int from, long long n_next, cudaStream
     return e;
 }
 
-int upload_tables(spin_batch* b, int chunk_planes) {
-    std::vector<int> tz;
-    b->host_items = make_items(&b->p, b->nrep, b->L.data(), chunk_planes, &tz);
+int class_of(const spin_batch* b, int L) {
+    for (size_t c = 0; c < b->cls_L.size(); ++c)
+        if (b->cls_L[c] == L) return (int)c;
+    return -1;
+}
+
+void drop_graphs(spin_batch* b) {
+    for (int q = 0; q < 2; ++q)
+        if (b->graph[q]) {
+            cudaGraphExecDestroy(b->graph[q]);
+            b->graph[q] = nullptr;
+        }
+}
+
+// Item and replica tables of the current class tiling, copied to the device
+// (synchronous); captured graphs hold the old launch shapes and are dropped.
+int upload_tables(spin_batch* b) {
+    std::vector<int> var_of(b->nrep), chunk_of(b->nrep), tz;
+    for (int r = 0; r < b->nrep; ++r) {
+        const int c = class_of(b, b->L[r]);
+        var_of[r] = b->cls_var[c];
+        chunk_of[r] = b->cls_chunk[c];
+    }
+    b->host_items = make_items(&b->p, b->nrep, b->L.data(), var_of, chunk_of, &tz, &b->var_first);
     b->nitems = (int)b->host_items.size();
-    const int S = b->tab.stages;
-    (void)S;
     b->host_reps.assign(b->nrep, BatchRep{});
     const double Dt = b->p.steps_per_pulse * std::fabs(b->p.dt);
     for (int r = 0; r < b->nrep; ++r) {
@@ -250,66 +306,96 @@ int upload_tables(spin_batch* b, int chunk_planes) {
         b->host_reps[r].tz = tz[r];
         b->host_reps[r].sigma = (float)std::sqrt(2.0 * b->p.lambda * b->T[r] * Dt);
     }
+    BATCH_CUDA(b, cudaStreamSynchronize(b->st));
     BATCH_CUDA(b, cudaMemcpy(b->items, b->host_items.data(), sizeof(BatchItem) * b->host_items.size(),
                              cudaMemcpyHostToDevice));
     BATCH_CUDA(b, cudaMemcpy(b->reps, b->host_reps.data(), sizeof(BatchRep) * b->host_reps.size(),
                              cudaMemcpyHostToDevice));
-    b->chunk_planes = chunk_planes;
+    drop_graphs(b);
+    b->eager_intervals = 0;
     return SPIN_OK;
 }
 
 std::mutex g_tune_mutex;
-std::map<std::string, int> g_tune_cache;
+std::map<std::string, std::pair<int, int>> g_tune_cache;   // class key -> (variant, chunk)
 
-std::string tune_key(const spin_batch* b) {
-    std::vector<int> Ls(b->L);
-    std::sort(Ls.begin(), Ls.end());
-    std::string k = "p" + std::to_string(b->p.precision) + "i" + std::to_string(b->p.integrator) + "L";
-    for (int v : Ls) k += std::to_string(v) + ",";
-    return k;
+std::string tune_key(const spin_batch* b, int L) {
+    return "p" + std::to_string(b->p.precision) + "i" + std::to_string(b->p.integrator) + "L" + std::to_string(L);
 }
 
-// Time each z-chunk candidate on the real tables (input buffer 0 -> buffer 1,
-// no pulse, so the caller's state is untouched) and keep the fastest.
-int autotune(spin_batch* b, int* best) {
+// Device time of one step over the current tables (input buffer 0 -> buffer
+// 1, no pulse, so the caller's state is untouched): the least of three.
+int time_step(spin_batch* b, cudaEvent_t e0, cudaEvent_t e1, float* ms_out) {
+    const StepLaunch<float> Ls = batch_launch_args(b, 0, false, b->st);
+    BATCH_CUDA(b, batch_step_kernels(b, Ls));
+    float ms_min = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {
+        BATCH_CUDA(b, cudaEventRecord(e0, b->st));
+        BATCH_CUDA(b, batch_step_kernels(b, Ls));
+        BATCH_CUDA(b, cudaEventRecord(e1, b->st));
+        BATCH_CUDA(b, cudaEventSynchronize(e1));
+        float ms = 0;
+        BATCH_CUDA(b, cudaEventElapsedTime(&ms, e0, e1));
+        ms_min = std::min(ms_min, ms);
+    }
+    *ms_out = ms_min;
+    return SPIN_OK;
+}
+
+// Per size class, one pass of coordinate descent on the whole batch: classes
+// in decreasing order of spins, each timed over every tile variant x z-chunk
+// candidate with the others held, keeping the fastest.  Pinned classes and
+// classes found in the process cache are held throughout.
+int autotune(spin_batch* b) {
+    const int nc = (int)b->cls_L.size();
+    std::vector<int> todo;
     {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
-        auto it = g_tune_cache.find(tune_key(b));
-        if (it != g_tune_cache.end()) {
-            *best = it->second;
-            return SPIN_OK;
+        for (int c = 0; c < nc; ++c) {
+            if (b->cls_pinned[c]) continue;
+            auto it = g_tune_cache.find(tune_key(b, b->cls_L[c]));
+            if (it != g_tune_cache.end()) {
+                b->cls_var[c] = it->second.first;
+                b->cls_chunk[c] = it->second.second;
+            } else {
+                todo.push_back(c);
+            }
         }
     }
+    std::vector<long long> spins(nc, 0);
+    for (int r = 0; r < b->nrep; ++r) spins[class_of(b, b->L[r])] += (long long)b->L[r] * b->L[r] * b->L[r];
+    std::stable_sort(todo.begin(), todo.end(), [&](int x, int y) { return spins[x] > spins[y]; });
     cudaEvent_t e0, e1;
     BATCH_CUDA(b, cudaEventCreate(&e0));
     BATCH_CUDA(b, cudaEventCreate(&e1));
-    float best_ms = 1e30f;
-    *best = kChunkCandidates[0];
-    for (int c : kChunkCandidates) {
-        int rc = upload_tables(b, c);
-        if (rc != SPIN_OK) return rc;
-        StepLaunch<float> Ls = batch_launch_args(b, 0, false, b->st);
-        BATCH_CUDA(b, launch_step_patch_batch(Ls, b->items, b->nitems, b->reps));
-        float ms_min = 1e30f;
-        for (int rep = 0; rep < 3; ++rep) {
-            BATCH_CUDA(b, cudaEventRecord(e0, b->st));
-            BATCH_CUDA(b, launch_step_patch_batch(Ls, b->items, b->nitems, b->reps));
-            BATCH_CUDA(b, cudaEventRecord(e1, b->st));
-            BATCH_CUDA(b, cudaEventSynchronize(e1));
-            float ms = 0;
-            BATCH_CUDA(b, cudaEventElapsedTime(&ms, e0, e1));
-            ms_min = std::min(ms_min, ms);
-        }
-        if (ms_min < best_ms) {
-            best_ms = ms_min;
-            *best = c;
-        }
+    int rc = SPIN_OK;
+    for (int c : todo) {
+        float best_ms = 1e30f;
+        int best_v = b->cls_var[c], best_k = b->cls_chunk[c];
+        for (int v = 0; v < patch_variants() && rc == SPIN_OK; ++v)
+            for (int k : kChunkCandidates) {
+                b->cls_var[c] = v;
+                b->cls_chunk[c] = k;
+                float ms = 0;
+                if ((rc = upload_tables(b)) != SPIN_OK || (rc = time_step(b, e0, e1, &ms)) != SPIN_OK) break;
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best_v = v;
+                    best_k = k;
+                }
+            }
+        b->cls_var[c] = best_v;
+        b->cls_chunk[c] = best_k;
+        if (rc != SPIN_OK) break;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    std::lock_guard<std::mutex> lock(g_tune_mutex);
-    g_tune_cache[tune_key(b)] = *best;
-    return SPIN_OK;
+    if (rc != SPIN_OK) return rc;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        for (int c : todo) g_tune_cache[tune_key(b, b->cls_L[c])] = {b->cls_var[c], b->cls_chunk[c]};
+    }
+    return upload_tables(b);
 }
 
 int capture_batch_interval(spin_batch* b, int from) {
@@ -366,7 +452,7 @@ int spin_batch_create(const spin_params* p, int32_t nrep, const int32_t* L, cons
     int v = validate_batch(p, nrep, L, T);
     if (v != SPIN_OK) return v;
     if (!T || !sx || !sy || !sz || !workspace || reinterpret_cast<uintptr_t>(workspace) % kAlign) return SPIN_EINVAL;
-    if (chunk_planes < 0) return SPIN_EINVAL;
+    if (chunk_planes < -1) return SPIN_EINVAL;
     const BLayout Lo = blayout(p, nrep, L);
     if (workspace_bytes < Lo.total) return SPIN_ENOSPACE;
     spin_batch* b = new (std::nothrow) spin_batch();
@@ -412,12 +498,15 @@ int spin_batch_create(const spin_params* p, int32_t nrep, const int32_t* L, cons
             rc = SPIN_ECUDA;
             break;
         }
-        int chosen = chunk_planes;
-        if (chosen == 0) {
-            if ((rc = upload_tables(b, kChunkCandidates[0])) != SPIN_OK) break;
-            if ((rc = autotune(b, &chosen)) != SPIN_OK) break;
-        }
-        rc = upload_tables(b, chosen);
+        // size classes in first-appearance order, default tiling
+        for (int r = 0; r < nrep; ++r)
+            if (class_of(b, L[r]) < 0) {
+                b->cls_L.push_back(L[r]);
+                b->cls_var.push_back(0);
+                b->cls_chunk.push_back(chunk_planes > 0 ? chunk_planes : kDefaultChunk);
+                b->cls_pinned.push_back(0);
+            }
+        rc = chunk_planes == 0 ? autotune(b) : upload_tables(b);
     } while (0);
     if (rc != SPIN_OK) {
         delete b;
@@ -429,9 +518,67 @@ int spin_batch_create(const spin_params* p, int32_t nrep, const int32_t* L, cons
 
 int spin_batch_tuning(const spin_batch* b, int32_t* chunk_planes, int32_t* nitems) {
     if (!b) return SPIN_EINVAL;
-    if (chunk_planes) *chunk_planes = b->chunk_planes;
+    if (chunk_planes) {
+        // the chunk of the class holding the most spins
+        long long best = -1;
+        for (size_t c = 0; c < b->cls_L.size(); ++c) {
+            long long n = 0;
+            for (int r = 0; r < b->nrep; ++r)
+                if (b->L[r] == b->cls_L[c]) n += (long long)b->L[r] * b->L[r] * b->L[r];
+            if (n > best) {
+                best = n;
+                *chunk_planes = b->cls_chunk[c];
+            }
+        }
+    }
     if (nitems) *nitems = b->nitems;
     return SPIN_OK;
+}
+
+int spin_batch_tile_rows(int32_t integrator, int32_t max, int32_t* rows, int32_t* n) {
+    if (!n || max < 0 || (max > 0 && !rows)) return SPIN_EINVAL;
+    const Tableau tb = tableau_for(integrator);
+    if (!tb.chain || !(tb.stages == 2 || tb.stages == 4)) return SPIN_EUNSUPPORTED;
+    *n = patch_variants();
+    for (int v = 0; v < std::min<int>(max, patch_variants()); ++v) rows[v] = patch_rows(tb.stages, v);
+    return SPIN_OK;
+}
+
+int spin_batch_tiling(const spin_batch* b, int32_t max, int32_t* L, int32_t* tile_rows, int32_t* chunk, int32_t* n) {
+    if (!b || !n || max < 0 || (max > 0 && (!L || !tile_rows || !chunk))) return SPIN_EINVAL;
+    const int nc = (int)b->cls_L.size();
+    *n = nc;
+    for (int c = 0; c < std::min<int>(max, nc); ++c) {
+        L[c] = b->cls_L[c];
+        tile_rows[c] = patch_rows(b->tab.stages, b->cls_var[c]);
+        chunk[c] = b->cls_chunk[c];
+    }
+    return SPIN_OK;
+}
+
+int spin_batch_set_tiling(spin_batch* b, int32_t n, const int32_t* L, const int32_t* tile_rows, const int32_t* chunk) {
+    if (!b || n < 0 || (n > 0 && (!L || !tile_rows || !chunk))) return SPIN_EINVAL;
+    std::vector<int> cls(n), var(n);
+    for (int q = 0; q < n; ++q) {
+        cls[q] = class_of(b, L[q]);
+        if (cls[q] < 0) return bset_err(b, SPIN_EINVAL, "no replica has side %d", L[q]);
+        var[q] = -1;
+        for (int v = 0; v < patch_variants(); ++v)
+            if (patch_rows(b->tab.stages, v) == tile_rows[q]) var[q] = v;
+        if (var[q] < 0) return bset_err(b, SPIN_EINVAL, "tile_rows %d is not offered for this integrator", tile_rows[q]);
+        if (chunk[q] < 1) return bset_err(b, SPIN_EINVAL, "chunk %d < 1", chunk[q]);
+    }
+    for (int q = 0; q < n; ++q) {
+        b->cls_var[cls[q]] = var[q];
+        b->cls_chunk[cls[q]] = chunk[q];
+        b->cls_pinned[cls[q]] = 1;
+    }
+    return upload_tables(b);
+}
+
+int spin_batch_autotune(spin_batch* b) {
+    if (!b) return SPIN_EINVAL;
+    return autotune(b);
 }
 
 int spin_batch_step_pulse(spin_batch* b, int64_t nsteps) {
@@ -507,8 +654,7 @@ int spin_batch_samples(spin_batch* b, double* out, int64_t max_records, int64_t*
 
 int spin_batch_destroy(spin_batch* b) {
     if (!b) return SPIN_EINVAL;
-    for (int q = 0; q < 2; ++q)
-        if (b->graph[q]) cudaGraphExecDestroy(b->graph[q]);
+    drop_graphs(b);
     if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
     delete b;
     return SPIN_OK;

@@ -69,8 +69,10 @@ cudaError_t prepare_step_kernels();
 // FP32 fused step with register patches (chain tableaus, 2 or 4 stages).
 cudaError_t launch_step_patch(const StepLaunch<float>& L);
 cudaError_t prepare_patch_kernels();
-int patch_out_x(int stages);   // output columns per CTA tile along x
-int patch_out_y(int stages);   // ... along y
+int patch_out_x(int stages);                // output columns per CTA tile along x
+int patch_out_y(int stages, int variant);   // ... along y, for tile variant 0 .. patch_variants()-1
+int patch_rows(int stages, int variant);    // tile rows (output rows + 2 x stages)
+int patch_variants();
 
 // Batched replicas (cubic periodic lattices, one concatenated SoA state).
 struct BatchItem {
@@ -86,7 +88,7 @@ struct BatchRep {
     int pad;
 };
 cudaError_t launch_step_patch_batch(const StepLaunch<float>& L, const BatchItem* items, int nitems,
-                                    const BatchRep* reps);
+                                    const BatchRep* reps, int variant);
 
 // Batched observables: block b reduces rows [row0, row0+nrows) of replica rep;
 // blocks of one replica are contiguous; first_block has nrep+1 entries.

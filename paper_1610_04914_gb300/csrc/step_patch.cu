@@ -32,21 +32,42 @@ constexpr int kPT = 16;        // threads along x
 constexpr int kPC = 2 * kPT;   // columns along x (two per thread, one float2)
 constexpr int kRS = kPC;       // shared row stride (floats)
 
-// Rows per thread (PY) and thread rows (TY) per stage count: RK4 keeps one row
-// per thread (register rings of 4 stage planes do not fit twice), RK2/Heun two.
-template <int S>
+// Rows per thread (PY) and thread rows (TY) per stage count and tile variant
+// V: RK4 keeps one row per thread (register rings of 4 stage planes do not fit
+// twice), RK2/Heun two.  Variant 0 is the single-lattice tile; the batched
+// replicas choose among the variants per replica size (the tile's output
+// height is PY*TY - 2S rows, and a replica of side L needs ceil(L/out) tiles
+// along y).
+template <int S, int V = 0>
 struct PatchShape;
 #ifndef SPIN_PATCH_TY4
 #define SPIN_PATCH_TY4 24
 #endif
 template <>
-struct PatchShape<4> {
+struct PatchShape<4, 0> {
     static constexpr int PY = 1, TY = SPIN_PATCH_TY4;
 };
 template <>
-struct PatchShape<2> {
+struct PatchShape<4, 1> {
+    static constexpr int PY = 1, TY = 20;
+};
+template <>
+struct PatchShape<4, 2> {
+    static constexpr int PY = 1, TY = 16;
+};
+template <>
+struct PatchShape<2, 0> {
     static constexpr int PY = 2, TY = 16;
 };
+template <>
+struct PatchShape<2, 1> {
+    static constexpr int PY = 2, TY = 12;
+};
+template <>
+struct PatchShape<2, 2> {
+    static constexpr int PY = 2, TY = 8;
+};
+constexpr int kTileVariants = 3;
 
 struct PatchArgs {
     const float* __restrict__ in0;
@@ -144,13 +165,13 @@ struct PThread {
 // cp.async (the thread only ever reads back its own columns): 4 slots x 3
 // components x PY rows, one column pair (two adjacent floats) per thread,
 // thread-minor, so the pair is one conflict-free 8-byte access.
-template <int S>
+template <int S, int V>
 __device__ __forceinline__ float* stage_pair(float* stg, int slot, int c, int rr, int tid) {
-    constexpr int PY = PatchShape<S>::PY, NT = kPT * PatchShape<S>::TY;
+    constexpr int PY = PatchShape<S, V>::PY, NT = kPT * PatchShape<S, V>::TY;
     return stg + 2 * ((((slot * 3 + c) * PY + rr) * NT) + tid);
 }
 
-template <int S>
+template <int S, int V>
 __device__ __forceinline__ void issue_plane(const PatchArgs& a, float* stg, const PThread<PatchShape<S>::PY>& th,
                                             int slot, int gz, int tid) {
     constexpr int PY = PatchShape<S>::PY;
@@ -159,9 +180,9 @@ __device__ __forceinline__ void issue_plane(const PatchArgs& a, float* stg, cons
 #pragma unroll
         for (int rr = 0; rr < PY; ++rr) {
             const int o = base + th.col[rr][0];
-            cp_async8(stage_pair<S>(stg, slot, 0, rr, tid), a.in0 + o);
-            cp_async8(stage_pair<S>(stg, slot, 1, rr, tid), a.in1 + o);
-            cp_async8(stage_pair<S>(stg, slot, 2, rr, tid), a.in2 + o);
+            cp_async8(stage_pair<S, V>(stg, slot, 0, rr, tid), a.in0 + o);
+            cp_async8(stage_pair<S, V>(stg, slot, 1, rr, tid), a.in1 + o);
+            cp_async8(stage_pair<S, V>(stg, slot, 2, rr, tid), a.in2 + o);
         }
     } else {
 #pragma unroll
@@ -169,19 +190,19 @@ __device__ __forceinline__ void issue_plane(const PatchArgs& a, float* stg, cons
 #pragma unroll
             for (int e = 0; e < 2; ++e) {
                 const int o = base + th.col[rr][e];
-                cp_async4(stage_pair<S>(stg, slot, 0, rr, tid) + e, a.in0 + o);
-                cp_async4(stage_pair<S>(stg, slot, 1, rr, tid) + e, a.in1 + o);
-                cp_async4(stage_pair<S>(stg, slot, 2, rr, tid) + e, a.in2 + o);
+                cp_async4(stage_pair<S, V>(stg, slot, 0, rr, tid) + e, a.in0 + o);
+                cp_async4(stage_pair<S, V>(stg, slot, 1, rr, tid) + e, a.in1 + o);
+                cp_async4(stage_pair<S, V>(stg, slot, 2, rr, tid) + e, a.in2 + o);
             }
     }
     cp_async_commit();
 }
 
-template <int S, bool PREC, bool HSITE, bool PULSE, bool STORE, int P>
+template <int S, bool PREC, bool HSITE, bool PULSE, bool STORE, int P, int V>
 __device__ __forceinline__ void patch_iteration(const PatchArgs& a, PRings<S, HSITE>& r, float* __restrict__ sh,
                                                 float* __restrict__ stg, PThread<PatchShape<S>::PY>& th, int i,
                                                 int t0, int z0, long long k, int tid) {
-    constexpr int PY = PatchShape<S>::PY, ROWS = PatchShape<S>::PY * PatchShape<S>::TY;
+    constexpr int PY = PatchShape<S, V>::PY, ROWS = PatchShape<S, V>::PY * PatchShape<S, V>::TY;
     constexpr int TILE = ROWS * kRS;
     float* shb = sh + (P & 1) * (S * 3 * TILE);
     const int cy0 = PY * th.ty;
@@ -204,7 +225,7 @@ __device__ __forceinline__ void patch_iteration(const PatchArgs& a, PRings<S, HS
     //    ago); plane t+S+2 is requested now
     const int t = i + t0;
     {
-        issue_plane<S>(a, stg, th, (P + S + 2) & 3, th.gz_issue, tid);
+        issue_plane<S, V>(a, stg, th, (P + S + 2) & 3, th.gz_issue, tid);
         th.gz_issue = th.gz_issue + 1 == a.nz ? 0 : th.gz_issue + 1;
         cp_async_wait<2>();
         const int slot = (P + S) & 3;
@@ -212,7 +233,7 @@ __device__ __forceinline__ void patch_iteration(const PatchArgs& a, PRings<S, HS
         for (int rr = 0; rr < PY; ++rr)
 #pragma unroll
             for (int c = 0; c < 3; ++c)
-                r.s[slot][rr][c] = *reinterpret_cast<const f2*>(stage_pair<S>(stg, slot, c, rr, tid));
+                r.s[slot][rr][c] = *reinterpret_cast<const f2*>(stage_pair<S, V>(stg, slot, c, rr, tid));
         if (a.bc) {
             // free boundaries: no spin outside the lattice (a zero spin stays
             // zero through every stage, so it never feeds the stencil)
@@ -416,9 +437,9 @@ __device__ __forceinline__ void patch_iteration(const PatchArgs& a, PRings<S, HS
 }
 
 // One CTA's tile: columns (bx, by) of the x-y tiling, z chunk bz.
-template <int S, bool PREC, bool HSITE, bool PULSE, bool STORE>
+template <int S, bool PREC, bool HSITE, bool PULSE, bool STORE, int V>
 __device__ __forceinline__ void patch_tile(const PatchArgs& a, int bx, int by, int bz, float* __restrict__ sh) {
-    constexpr int PY = PatchShape<S>::PY, ROWS = PatchShape<S>::PY * PatchShape<S>::TY;
+    constexpr int PY = PatchShape<S, V>::PY, ROWS = PatchShape<S, V>::PY * PatchShape<S, V>::TY;
     float* stg = sh + 2 * S * 3 * ROWS * kRS;
     const int tid = threadIdx.y * kPT + threadIdx.x;
     PThread<PY> th;
@@ -481,27 +502,27 @@ __device__ __forceinline__ void patch_tile(const PatchArgs& a, int bx, int by, i
         }
     }
     // planes S and S+1 (local) go to the staging ring before the march
-    issue_plane<S>(a, stg, th, S & 3, wrapi(t0 + S, a.nz), tid);
-    issue_plane<S>(a, stg, th, (S + 1) & 3, wrapi(t0 + S + 1, a.nz), tid);
+    issue_plane<S, V>(a, stg, th, S & 3, wrapi(t0 + S, a.nz), tid);
+    issue_plane<S, V>(a, stg, th, (S + 1) & 3, wrapi(t0 + S + 1, a.nz), tid);
     th.gz_issue = wrapi(t0 + S + 2, a.nz);
     th.gz_field = wrapi(t0 + S - 1, a.nz);
     int i = 0;
     for (; i + 4 <= a.n_iter; i += 4) {
-        patch_iteration<S, PREC, HSITE, PULSE, STORE, 0>(a, r, sh, stg, th, i + 0, t0, z0, k, tid);
-        patch_iteration<S, PREC, HSITE, PULSE, STORE, 1>(a, r, sh, stg, th, i + 1, t0, z0, k, tid);
-        patch_iteration<S, PREC, HSITE, PULSE, STORE, 2>(a, r, sh, stg, th, i + 2, t0, z0, k, tid);
-        patch_iteration<S, PREC, HSITE, PULSE, STORE, 3>(a, r, sh, stg, th, i + 3, t0, z0, k, tid);
+        patch_iteration<S, PREC, HSITE, PULSE, STORE, 0, V>(a, r, sh, stg, th, i + 0, t0, z0, k, tid);
+        patch_iteration<S, PREC, HSITE, PULSE, STORE, 1, V>(a, r, sh, stg, th, i + 1, t0, z0, k, tid);
+        patch_iteration<S, PREC, HSITE, PULSE, STORE, 2, V>(a, r, sh, stg, th, i + 2, t0, z0, k, tid);
+        patch_iteration<S, PREC, HSITE, PULSE, STORE, 3, V>(a, r, sh, stg, th, i + 3, t0, z0, k, tid);
     }
-    if (i < a.n_iter) patch_iteration<S, PREC, HSITE, PULSE, STORE, 0>(a, r, sh, stg, th, i + 0, t0, z0, k, tid);
-    if (i + 1 < a.n_iter) patch_iteration<S, PREC, HSITE, PULSE, STORE, 1>(a, r, sh, stg, th, i + 1, t0, z0, k, tid);
-    if (i + 2 < a.n_iter) patch_iteration<S, PREC, HSITE, PULSE, STORE, 2>(a, r, sh, stg, th, i + 2, t0, z0, k, tid);
+    if (i < a.n_iter) patch_iteration<S, PREC, HSITE, PULSE, STORE, 0, V>(a, r, sh, stg, th, i + 0, t0, z0, k, tid);
+    if (i + 1 < a.n_iter) patch_iteration<S, PREC, HSITE, PULSE, STORE, 1, V>(a, r, sh, stg, th, i + 1, t0, z0, k, tid);
+    if (i + 2 < a.n_iter) patch_iteration<S, PREC, HSITE, PULSE, STORE, 2, V>(a, r, sh, stg, th, i + 2, t0, z0, k, tid);
     cp_async_wait<0>();   // no copy may land in shared memory after the tile is done
 }
 
 template <int S, bool PREC, bool HSITE, bool PULSE>
 __global__ void __launch_bounds__(kPT* PatchShape<S>::TY, 1) k_step_patch(PatchArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    patch_tile<S, PREC, HSITE, PULSE, false>(a, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z,
+    patch_tile<S, PREC, HSITE, PULSE, false, 0>(a, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z,
                                              reinterpret_cast<float*>(smem_raw));
 }
 
@@ -510,7 +531,7 @@ __global__ void __launch_bounds__(kPT* PatchShape<S>::TY, 1) k_step_patch(PatchA
 template <int S, bool PREC, bool HSITE>
 __global__ void __launch_bounds__(kPT* PatchShape<S>::TY, 1) k_step_patch_store(PatchArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    patch_tile<S, PREC, HSITE, false, true>(a, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z,
+    patch_tile<S, PREC, HSITE, false, true, 0>(a, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z,
                                             reinterpret_cast<float*>(smem_raw));
 }
 
@@ -518,8 +539,8 @@ __global__ void __launch_bounds__(kPT* PatchShape<S>::TY, 1) k_step_patch_store(
 // of a table sorted by cost; each replica is a cubic periodic lattice of side
 // L at its own offset in the concatenated arrays, with its own pulse angle
 // scale (temperature) and its index as the noise counter's replica word.
-template <int S, bool PREC, bool PULSE>
-__global__ void __launch_bounds__(kPT* PatchShape<S>::TY, 1)
+template <int S, bool PREC, bool PULSE, int V>
+__global__ void __launch_bounds__(kPT* PatchShape<S, V>::TY, 1)
     k_step_patch_batch(PatchArgs base, const BatchItem* __restrict__ items, const BatchRep* __restrict__ reps) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const BatchItem it = items[blockIdx.x];
@@ -538,13 +559,13 @@ __global__ void __launch_bounds__(kPT* PatchShape<S>::TY, 1)
     a.n_iter = rp.tz + 2 * S - 2;
     a.sigma = rp.sigma;
     a.replica = (uint64_t)it.rep;
-    patch_tile<S, PREC, false, PULSE, false>(a, it.bx, it.by, it.bz, reinterpret_cast<float*>(smem_raw));
+    patch_tile<S, PREC, false, PULSE, false, V>(a, it.bx, it.by, it.bz, reinterpret_cast<float*>(smem_raw));
 }
 
-template <int S, bool PREC, bool HSITE, bool PULSE>
+template <int S, bool PREC, bool HSITE, bool PULSE, int V = 0>
 size_t patch_smem() {
-    constexpr int ROWS = PatchShape<S>::PY * PatchShape<S>::TY, NT = kPT * PatchShape<S>::TY;
-    return sizeof(float) * (2 * S * 3 * ROWS * kRS + 4 * 3 * PatchShape<S>::PY * 2 * NT);
+    constexpr int ROWS = PatchShape<S, V>::PY * PatchShape<S, V>::TY, NT = kPT * PatchShape<S, V>::TY;
+    return sizeof(float) * (2 * S * 3 * ROWS * kRS + 4 * 3 * PatchShape<S, V>::PY * 2 * NT);
 }
 
 template <int S, bool PREC, bool HSITE, bool PULSE>
@@ -603,31 +624,49 @@ cudaError_t patch_dispatch(const PatchArgs& a, dim3 grid, cudaStream_t st, bool 
     return prepare ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-template <int S, bool PREC, bool PULSE>
+template <int S, bool PREC, bool PULSE, int V>
 cudaError_t batch_launch(const PatchArgs& a, const BatchItem* items, int nitems, const BatchRep* reps, cudaStream_t st,
                          bool prepare) {
-    const size_t smem = patch_smem<S, PREC, false, PULSE>();
+    const size_t smem = patch_smem<S, PREC, false, PULSE, V>();
     if (prepare)
-        return cudaFuncSetAttribute(k_step_patch_batch<S, PREC, PULSE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        return cudaFuncSetAttribute(k_step_patch_batch<S, PREC, PULSE, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem);
-    k_step_patch_batch<S, PREC, PULSE><<<nitems, dim3(kPT, PatchShape<S>::TY), smem, st>>>(a, items, reps);
+    if (nitems <= 0) return cudaSuccess;
+    k_step_patch_batch<S, PREC, PULSE, V><<<nitems, dim3(kPT, PatchShape<S, V>::TY), smem, st>>>(a, items, reps);
     return cudaGetLastError();
+}
+
+template <int S, int V>
+cudaError_t batch_dispatch_v(const PatchArgs& a, const BatchItem* items, int nitems, const BatchRep* reps,
+                             cudaStream_t st, bool prec, bool pulse, bool prepare) {
+    if (prepare) {
+        cudaError_t e;
+        if ((e = batch_launch<S, true, false, V>(a, items, nitems, reps, st, true)) != cudaSuccess) return e;
+        if ((e = batch_launch<S, true, true, V>(a, items, nitems, reps, st, true)) != cudaSuccess) return e;
+        if ((e = batch_launch<S, false, false, V>(a, items, nitems, reps, st, true)) != cudaSuccess) return e;
+        return batch_launch<S, false, true, V>(a, items, nitems, reps, st, true);
+    }
+    if (prec) return pulse ? batch_launch<S, true, true, V>(a, items, nitems, reps, st, false)
+                           : batch_launch<S, true, false, V>(a, items, nitems, reps, st, false);
+    return pulse ? batch_launch<S, false, true, V>(a, items, nitems, reps, st, false)
+                 : batch_launch<S, false, false, V>(a, items, nitems, reps, st, false);
 }
 
 template <int S>
 cudaError_t batch_dispatch(const PatchArgs& a, const BatchItem* items, int nitems, const BatchRep* reps,
-                           cudaStream_t st, bool prec, bool pulse, bool prepare) {
+                           cudaStream_t st, bool prec, bool pulse, bool prepare, int variant) {
     if (prepare) {
         cudaError_t e;
-        if ((e = batch_launch<S, true, false>(a, items, nitems, reps, st, true)) != cudaSuccess) return e;
-        if ((e = batch_launch<S, true, true>(a, items, nitems, reps, st, true)) != cudaSuccess) return e;
-        if ((e = batch_launch<S, false, false>(a, items, nitems, reps, st, true)) != cudaSuccess) return e;
-        return batch_launch<S, false, true>(a, items, nitems, reps, st, true);
+        if ((e = batch_dispatch_v<S, 0>(a, items, nitems, reps, st, prec, pulse, true)) != cudaSuccess) return e;
+        if ((e = batch_dispatch_v<S, 1>(a, items, nitems, reps, st, prec, pulse, true)) != cudaSuccess) return e;
+        return batch_dispatch_v<S, 2>(a, items, nitems, reps, st, prec, pulse, true);
     }
-    if (prec) return pulse ? batch_launch<S, true, true>(a, items, nitems, reps, st, false)
-                           : batch_launch<S, true, false>(a, items, nitems, reps, st, false);
-    return pulse ? batch_launch<S, false, true>(a, items, nitems, reps, st, false)
-                 : batch_launch<S, false, false>(a, items, nitems, reps, st, false);
+    switch (variant) {
+        case 0: return batch_dispatch_v<S, 0>(a, items, nitems, reps, st, prec, pulse, false);
+        case 1: return batch_dispatch_v<S, 1>(a, items, nitems, reps, st, prec, pulse, false);
+        case 2: return batch_dispatch_v<S, 2>(a, items, nitems, reps, st, prec, pulse, false);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 PatchArgs patch_args_common(const StepLaunch<float>& L) {
@@ -717,24 +756,30 @@ cudaError_t launch_pulse_batch(float* s[3], const BatchRep* reps, const ObsBlock
 }
 
 int patch_out_x(int stages) { return kPC - 2 * stages; }
-int patch_out_y(int stages) {
-    return (stages == 4 ? PatchShape<4>::PY * PatchShape<4>::TY : PatchShape<2>::PY * PatchShape<2>::TY) - 2 * stages;
+int patch_rows(int stages, int variant) {
+    if (stages == 4)
+        return variant == 1 ? PatchShape<4, 1>::TY : (variant == 2 ? PatchShape<4, 2>::TY : PatchShape<4, 0>::TY);
+    return PatchShape<2, 0>::PY *
+           (variant == 1 ? PatchShape<2, 1>::TY : (variant == 2 ? PatchShape<2, 2>::TY : PatchShape<2, 0>::TY));
 }
+int patch_out_y(int stages, int variant) { return patch_rows(stages, variant) - 2 * stages; }
+int patch_variants() { return kTileVariants; }
 
 cudaError_t launch_step_patch_batch(const StepLaunch<float>& L, const BatchItem* items, int nitems,
-                                    const BatchRep* reps) {
+                                    const BatchRep* reps, int variant) {
     const PatchArgs a = patch_args_common(L);
     const bool prec = L.precession != 0;
-    if (L.tab->stages == 4) return batch_dispatch<4>(a, items, nitems, reps, L.stream, prec, L.pulse != 0, false);
-    return batch_dispatch<2>(a, items, nitems, reps, L.stream, prec, L.pulse != 0, false);
+    if (L.tab->stages == 4)
+        return batch_dispatch<4>(a, items, nitems, reps, L.stream, prec, L.pulse != 0, false, variant);
+    return batch_dispatch<2>(a, items, nitems, reps, L.stream, prec, L.pulse != 0, false, variant);
 }
 
 cudaError_t prepare_patch_kernels() {
     {
         PatchArgs a{};
-        cudaError_t e = batch_dispatch<4>(a, nullptr, 0, nullptr, 0, false, false, true);
+        cudaError_t e = batch_dispatch<4>(a, nullptr, 0, nullptr, 0, false, false, true, 0);
         if (e != cudaSuccess) return e;
-        e = batch_dispatch<2>(a, nullptr, 0, nullptr, 0, false, false, true);
+        e = batch_dispatch<2>(a, nullptr, 0, nullptr, 0, false, false, true, 0);
         if (e != cudaSuccess) return e;
     }
     PatchArgs a{};
@@ -751,7 +796,7 @@ cudaError_t launch_step_patch(const StepLaunch<float>& L) {
     const int S = L.tab->stages;
     PatchArgs a = patch_args_common(L);
     const int outx = kPC - 2 * S;
-    const int outy = (S == 4 ? PatchShape<4>::PY * PatchShape<4>::TY : PatchShape<2>::PY * PatchShape<2>::TY) - 2 * S;
+    const int outy = patch_out_y(S, 0);
     const int tiles_x = (L.g.nx + outx - 1) / outx;
     const int tiles_y = (L.g.ny + outy - 1) / outy;
     // z chunks: one resident CTA per SM, so pick the chunk count that

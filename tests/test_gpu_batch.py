@@ -54,15 +54,67 @@ def test_batch_bitwise_equals_single_lattices(gpu, precession, integrator):
         assert np.allclose(ob[:3], M, rtol=0, atol=1e-12) and abs(ob[3] - E) < 1e-12
 
 
-def test_batch_tiling_does_not_change_results(gpu):
-    L, T = [32, 24, 16], [1.0, 0.5, 1.5]
-    _, _, a = _batch(gpu, L, T, chunk=8)
-    _, _, b = _batch(gpu, L, T, chunk=64)
-    _, _, c = _batch(gpu, L, T, chunk=None)   # autotuned
-    assert c.chunk_planes in (8, 16, 32, 64)
-    for x in (a, b, c):
-        x.step(20)
-    assert torch.equal(a.state, b.state) and torch.equal(a.state, c.state)
+@pytest.mark.parametrize("integrator", [0, 2])
+def test_batch_tiling_does_not_change_results(gpu, integrator):
+    """Every tile height the library offers x z-chunks from 3 planes to
+    whole-lattice, the same tiling for all classes and a different one per
+    class (several launches per step), and the autotuned choice: the states
+    after 20 steps (graph replays and a partial interval) are bit-identical."""
+    L, T = [32, 24, 16, 24, 9], [1.0, 0.5, 1.5, 0.7, 1.1]
+    rows = gpu.spin_batch_tile_rows(integrator)
+    assert len(rows) == 3 and rows == sorted(rows, reverse=True)
+    _, _, ref = _batch(gpu, L, T, chunk=gpu.batch.DEFAULT_TILING, integrator=integrator)
+    ref.step(20)
+    for tr in rows:
+        for ch in (3, 8, 64):
+            _, _, b = _batch(gpu, L, T, chunk=gpu.batch.DEFAULT_TILING, integrator=integrator)
+            b.set_tiling({l: (tr, ch) for l in set(L)})
+            assert b.tiling() == {l: (tr, ch) for l in (32, 24, 16, 9)}
+            b.step(20)
+            assert torch.equal(ref.state, b.state), (tr, ch)
+            b.close()
+    mixed = {32: (rows[0], 5), 24: (rows[1], 16), 16: (rows[2], 8), 9: (rows[1], 64)}
+    _, _, m = _batch(gpu, L, T, chunk=gpu.batch.DEFAULT_TILING, integrator=integrator)
+    m.set_tiling(mixed)
+    m.step(20)
+    assert torch.equal(ref.state, m.state)
+    _, _, c = _batch(gpu, L, T, chunk=None, integrator=integrator)   # autotuned
+    t = c.tiling()
+    assert set(t) == {32, 24, 16, 9}
+    assert all(r in rows and k in (8, 16, 32, 64) for r, k in t.values())
+    c.step(20)
+    assert torch.equal(ref.state, c.state)
+
+
+def test_batch_tiling_rejects_bad_requests(gpu):
+    _, _, b = _batch(gpu, [16, 8], [1.0, 1.0], chunk=gpu.batch.DEFAULT_TILING)
+    rows = gpu.spin_batch_tile_rows(0)
+    with pytest.raises(gpu.SpinError):
+        b.set_tiling({12: (rows[0], 8)})        # no replica of side 12
+    with pytest.raises(gpu.SpinError):
+        b.set_tiling({16: (rows[0] + 1, 8)})    # height not offered
+    with pytest.raises(gpu.SpinError):
+        b.set_tiling({16: (rows[0], 0)})        # empty chunk
+    assert b.tiling() == {16: (rows[0], 32), 8: (rows[0], 32)}
+
+
+def test_batch_tiling_cache_is_per_size_class(gpu, tmp_path, monkeypatch):
+    """The JSON cache holds one entry per (precision, integrator, L); a later
+    batch with another mix of sizes reuses the classes it shares."""
+    monkeypatch.setenv("XDG_CACHE_HOME", str(tmp_path))
+    p = gpu.Params(1, 1, 1, **KW)
+    st = lambda L: [spin_inputs.random_spins(l, l, l, seed=3 + r) for r, l in enumerate(L)]
+    a = gpu.Batch(p, [16, 24], [1.0, 1.0], st([16, 24]))
+    import json
+    cache = json.load(open(tmp_path / "spinpulse" / "batch_tiling.json"))
+    assert set(cache) == {"p32-i0-L16", "p32-i0-L24"}
+    assert {int(k.split("L")[-1]): tuple(v) for k, v in cache.items()} == a.tiling()
+    forced = {"p32-i0-L16": [gpu.spin_batch_tile_rows(0)[2], 3]}
+    json.dump({**cache, **forced}, open(tmp_path / "spinpulse" / "batch_tiling.json", "w"))
+    b = gpu.Batch(p, [16, 32], [1.0, 1.0], st([16, 32]))
+    assert b.tiling()[16] == tuple(forced["p32-i0-L16"])
+    cache = json.load(open(tmp_path / "spinpulse" / "batch_tiling.json"))
+    assert set(cache) == {"p32-i0-L16", "p32-i0-L24", "p32-i0-L32"}
 
 
 def test_batch_full_size_512_replicas(gpu):
