@@ -69,6 +69,13 @@ cudaError_t prepare_step_kernels();
 // FP32 fused step with register patches (chain tableaus, 2 or 4 stages).
 cudaError_t launch_step_patch(const StepLaunch<float>& L);
 cudaError_t prepare_patch_kernels();
+// The noise rotation of Eq. (s_rotation) over every site of L.out, in place.
+cudaError_t launch_pulse_lattice(const StepLaunch<float>& L);
+// FP32 fused six-stage (Butcher RK5) step in two three-stage segments; needs
+// L.tmp with 12N floats (the four carried vectors) and no per-site field.
+bool rk5_fused_supports(const StepLaunch<float>& L);
+cudaError_t launch_step_rk5(const StepLaunch<float>& L);
+cudaError_t prepare_rk5_kernels();
 int patch_out_x(int stages);                // output columns per CTA tile along x
 int patch_out_y(int stages, int variant);   // ... along y, for tile variant 0 .. patch_variants()-1
 int patch_rows(int stages, int variant);    // tile rows (output rows + 2 x stages)

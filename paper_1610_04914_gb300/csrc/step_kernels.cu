@@ -11,7 +11,9 @@
 //    memory, z neighbours from per-thread register rings) and writes the
 //    finished plane t.  Stage states never leave the SM: one read and one
 //    write of the state per step.
-//  * any tableau (Butcher RK5): one stencil kernel per stage plus a combine
+//  * Butcher RK5 in FP32 without a per-site field: two fused three-stage
+//    segments (step_rk5.cu).
+//  * any tableau, any precision: one stencil kernel per stage plus a combine
 //    kernel, stage states in the workspace.
 #include <cuda_runtime.h>
 
@@ -325,7 +327,8 @@ cudaError_t prepare_step_kernels() {
     if (e != cudaSuccess) return e;
     e = dispatch_chain<real, 2, BX, BY>(a, dim3(1), 0, false, false, false, true);
     if (e != cudaSuccess || sizeof(real) != 4) return e;
-    return prepare_patch_kernels();
+    if ((e = prepare_patch_kernels()) != cudaSuccess) return e;
+    return prepare_rk5_kernels();
 }
 template cudaError_t prepare_step_kernels<float>();
 template cudaError_t prepare_step_kernels<double>();
@@ -563,6 +566,8 @@ cudaError_t launch_step(const StepLaunch<real>& L) {
         if (sizeof(real) == 4) return launch_step_patch(reinterpret_cast<const StepLaunch<float>&>(L));
         return launch_chain<real>(L);
     }
+    if (sizeof(real) == 4 && !L.force_generic && rk5_fused_supports(reinterpret_cast<const StepLaunch<float>&>(L)))
+        return launch_step_rk5(reinterpret_cast<const StepLaunch<float>&>(L));
     return launch_generic<real>(L);
 }
 

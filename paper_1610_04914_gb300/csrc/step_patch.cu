@@ -21,16 +21,13 @@
 
 #include <algorithm>
 
+#include "patch_common.cuh"
 #include "spin_device.cuh"
 #include "spin_internal.h"
 
 namespace spin {
 
 namespace {
-
-constexpr int kPT = 16;        // threads along x
-constexpr int kPC = 2 * kPT;   // columns along x (two per thread, one float2)
-constexpr int kRS = kPC;       // shared row stride (floats)
 
 // Rows per thread (PY) and thread rows (TY) per stage count and tile variant
 // V: RK4 keeps one row per thread (register rings of 4 stage planes do not fit
@@ -100,46 +97,6 @@ struct PatchArgs {
     float dt;
     int* err;          // device status word for bounded waits (nullable; no wait in this kernel sets it)
 };
-
-// A column pair (2m, 2m+1) is contiguous in a row of even length and never
-// straddles the periodic wrap; with 8-byte aligned component arrays it can be
-// fetched as one 8-byte copy.
-__host__ __device__ __forceinline__ bool pairs_aligned(int nx, const float* p0, const float* p1, const float* p2) {
-    return (nx & 1) == 0 && ((reinterpret_cast<unsigned long long>(p0) | reinterpret_cast<unsigned long long>(p1) |
-                              reinterpret_cast<unsigned long long>(p2)) & 7ULL) == 0;
-}
-
-typedef float2 f2;
-#ifndef SPIN_NO_F32X2
-__device__ __forceinline__ f2 add2(f2 a, f2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ f2 mul2(f2 a, f2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
-#else
-// scalar FP32 per component (tuning comparison)
-__device__ __forceinline__ f2 add2(f2 a, f2 b) { return make_float2(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y)); }
-__device__ __forceinline__ f2 mul2(f2 a, f2 b) { return make_float2(__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y)); }
-__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return make_float2(__fmaf_rn(a.x, b.x, c.x), __fmaf_rn(a.y, b.y, c.y)); }
-#endif
-__device__ __forceinline__ f2 sp2(float v) { return make_float2(v, v); }
-
-__device__ __forceinline__ void cp_async4(float* smem, const float* gmem) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async8(float* smem, const float* gmem) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
-__device__ __forceinline__ int wrapi(int v, int n) {
-    int r = v % n;
-    return r < 0 ? r + n : r;
-}
 
 template <int S, bool HSITE>
 struct PRings {
@@ -838,6 +795,10 @@ cudaError_t launch_step_patch(const StepLaunch<float>& L) {
                    : patch_dispatch<2>(a, grid, L.stream, prec, hs, false, false);
     }
     if (e != cudaSuccess || !L.pulse) return e;
+    return launch_pulse_lattice(L);
+}
+
+cudaError_t launch_pulse_lattice(const StepLaunch<float>& L) {
     const long long N = L.g.N();
     const int blocks = (int)std::max<long long>(1, std::min<long long>((N + 255) / 256, 152LL * 8));
     k_pulse_f32<<<blocks, 256, 0, L.stream>>>(L.out[0], L.out[1], L.out[2], N, L.seed, L.d_interval, L.replica,

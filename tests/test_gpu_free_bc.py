@@ -22,6 +22,10 @@ CASES = [  # size, precision, integrator, precession, h_site, path
     # rows of 64 / 128 columns: no spin beyond the first and last column
     ((64, 19, 9), 32, 0, 1, False, 0),
     ((128, 9, 11), 32, 0, 0, False, 0),
+    # Butcher RK5, fused two-segment FP32 path
+    ((20, 19, 18), 32, 1, 1, False, 0),
+    ((2, 3, 5), 32, 1, 0, False, 0),
+    ((64, 19, 9), 32, 1, 1, False, 0),
 ]
 
 

@@ -64,14 +64,24 @@ CASES = [
     ((128, 10, 7), 32, 0, 1, False, 0),
     ((64, 30, 21), 32, 0, 0, False, 0),
     ((64, 17, 40), 32, 0, 1, False, 0),
+    # Butcher RK5 on the fused two-segment path (FP32, no h_i): ragged, tiny,
+    # one site, several tiles along x and y, and a 128-column row
+    ((20, 19, 18), 32, 1, 0, False, 0),
+    ((37, 21, 13), 32, 1, 1, False, 0),
+    ((2, 3, 5), 32, 1, 1, False, 0),
+    ((1, 1, 1), 32, 1, 0, False, 0),
+    ((64, 30, 21), 32, 1, 1, False, 0),
+    ((128, 10, 7), 32, 1, 0, False, 0),
+    ((20, 19, 18), 32, 1, 1, False, 1),
 ]
 
 
 @pytest.mark.parametrize("shape,prec,integ,precession,hsite,path", CASES)
 def test_three_steps_with_pulse(gpu, orc, shape, prec, integ, precession, hsite, path):
     """Three steps with R = 3: a pulse after step 1 (mid-interval), a sample
-    after step 3; fused kernels (RK4, RK2, Heun) and per-stage kernels (RK5,
-    forced path 1), ragged and tiny lattices, with and without h_i."""
+    after step 3; fused kernels (RK4, RK2, Heun; RK5 in two segments) and
+    per-stage kernels (RK5 with h_i or in FP64, forced path 1), ragged and tiny
+    lattices, with and without h_i."""
     nx, ny, nz = shape
     p = gpu.Params(nx, ny, nz, J=0.9, D=0.15, H=(0.05, -0.1, 0.2), lam=0.1, T=0.7, dt=0.07, R=3,
                    integrator=integ, precession=precession, seed=77, replica=2, precision=prec, path=path)
@@ -278,3 +288,38 @@ def test_applicability_warning(gpu):
     assert lat.status == gpu.SPIN_WARN_APPLICABILITY
     q = gpu.Params(n, n, n, lam=0.01, T=1.0, dt=0.2, R=10, precision=32)
     assert gpu.Lattice(q, torch.from_numpy(spin_inputs.random_spins(n, n, n, seed=1))).status == gpu.SPIN_OK
+
+
+@pytest.mark.parametrize("bc", [0, 1])
+def test_rk5_fused_trajectory(gpu, orc, bc):
+    """Butcher RK5 in FP32 on the fused two-segment path, 40^3 (several tiles
+    and z-chunks), dt = 0.15, pulses every 10 steps.  Each of the first 10
+    steps, restarted in the oracle from the GPU state, within 5e-6 (measured
+    3.5e-6 for this path and for the per-stage FP32 path alike); after 30
+    steps the fused path, the per-stage FP32 path (forced path 1) and the
+    oracle within 6e-5 of each other (measured 3.2e-5: the FP32 step error
+    grows by about 10x over 30 steps, the same for both FP32 paths)."""
+    n = 40
+    kw = dict(J=1.0, D=0.05, H=(0.02, 0.0, 0.1), lam=0.05, T=0.9, dt=0.15, R=10, seed=21, integrator=gpu.RK5_BUTCHER,
+              precision=32, bc=bc)
+    p = gpu.Params(n, n, n, **kw)
+    s0 = spin_inputs.random_spins(n, n, n, seed=5)
+    lat = gpu.Lattice(p, torch.from_numpy(s0))
+    cur = gpu_state(lat)
+    worst = 0.0
+    for step in range(10):
+        lat.step(1)
+        nxt = gpu_state(lat)
+        ref1, _ = run_oracle(orc, p, cur, 1, n0=step)
+        worst = max(worst, float(np.max(np.abs(nxt - ref1))))
+        cur = nxt
+    assert worst < 5e-6, worst
+    lat.step(20)
+    got = gpu_state(lat)
+    per_stage, _ = run_gpu(gpu, gpu.Params(n, n, n, path=1, **kw), s0, 30)
+    ref, smp = run_oracle(orc, p, s0, 30)
+    assert np.max(np.abs(got - ref)) < 6e-5
+    assert np.max(np.abs(per_stage - ref)) < 6e-5
+    assert np.max(np.abs(got - per_stage)) < 6e-5
+    rec = np.array(lat.samples())
+    assert rec.shape == (3, 5) and np.max(np.abs(rec[:, 1:] - smp[:, 1:])) < 5e-6
