@@ -395,19 +395,22 @@ def adjoint_timing(sp, torch, dev, precision=32, steps=None):
     s0 = spin_inputs.random_spins(nx, ny, nz, seed=w["spin_seed"])
     hs = spin_inputs.site_fields(nx, ny, nz, w["field_sigma"], seed=w["noise_seed"])
     n, K = (steps or w["steps"]), w["checkpoint"]
-    lat = sp.Lattice(p, torch.from_numpy(s0), h_site=torch.from_numpy(hs), device=dev)
-    lat.record(K, n)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    lat.step(n)
-    M, E = lat.observables()
-    t1 = time.perf_counter()
-    dLdM = [2.0 * (M[a] - w["m_target"][a]) for a in range(3)]
-    g = lat.backward(dLdM, 1.0, field_grad=True)
-    torch.cuda.synchronize()
-    t2 = time.perf_counter()
-    gh = g["h"].double().cpu().numpy()
-    lat.close()
+    # the whole run twice: the first builds the library's graphs and warms the
+    # allocator's cache, the second is timed
+    for _ in range(2):
+        lat = sp.Lattice(p, torch.from_numpy(s0), h_site=torch.from_numpy(hs), device=dev)
+        lat.record(K, n)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lat.step(n)
+        M, E = lat.observables()
+        t1 = time.perf_counter()
+        dLdM = [2.0 * (M[a] - w["m_target"][a]) for a in range(3)]
+        g = lat.backward(dLdM, 1.0, field_grad=True)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        gh = g["h"].double().cpu().numpy()
+        lat.close()
     return {"workload": f"64^3 FP{precision} RK4, {n} steps, pulse every 10, checkpoint every 50, "
                         "loss E + |M - m*|^2",
             "fwd_ms_per_step": 1e3 * (t1 - t0) / n, "adjoint_ms_per_step": 1e3 * (t2 - t1) / n,
@@ -826,6 +829,9 @@ def run_ours(args, ws, rank, local):
             "metropolis_vs_pulse": mc,
             "wall_s_timed_region": wall,
             "cpu_baseline": cpu,
+            # the metric's third part, repeated last so that a reader of the
+            # line's tail sees it: 64^3 FP32 forward + checkpointed adjoint
+            "fwd_plus_adjoint_ms_per_step": adj["fwd_plus_adjoint_ms_per_step"] if adj else None,
         }
         print(json.dumps(line), flush=True)
     lat.close()
