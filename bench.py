@@ -201,7 +201,7 @@ class ClockSampler:
 
 
 # the sources k_step_patch is compiled from (its own file and the headers it includes)
-PATCH_KERNEL_SOURCES = ("step_patch.cu", "spin_device.cuh", "spin_internal.h")
+PATCH_KERNEL_SOURCES = ("step_patch.cu", "patch_common.cuh", "spin_device.cuh", "spin_internal.h")
 
 
 def _kernel_source_hash():
