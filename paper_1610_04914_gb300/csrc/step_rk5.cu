@@ -24,9 +24,12 @@
 // and one lane per row stores the row (24 records) with one bulk copy; in B
 // one lane per row fetches the row's 32 records (one or two runs where the
 // row wraps around x) into a 4-slot ring, counted on the slot's mbarrier.
-// Along x the tile keeps a halo of 4 columns (3 would do), so that with rows
-// of even length every thread's column pair is one aligned 8-byte word of the
-// state arrays.  HBM traffic per site and step: 12 + 48 bytes for A, 48 + 12
+// Along x the tile needs a halo of 3 columns, like along y; its first column
+// sits 4 columns left of the output window, at an even column, so that with
+// rows of even length every thread's column pair is one aligned 8-byte word
+// of the state arrays, and its output window is the 26 columns from tile
+// column 3 (tile bx outputs global columns 26 bx - 1 .. 26 bx + 24, clipped to
+// the lattice).  HBM traffic per site and step: 12 + 48 bytes for A, 48 + 12
 // for B.
 #include <cuda_runtime.h>
 
@@ -40,14 +43,14 @@ namespace spin {
 
 namespace {
 
-constexpr int kH = 3;    // stages per segment = tile halo along y
-constexpr int kHX = 4;   // tile halo along x (even: aligned column pairs)
+constexpr int kH = 3;    // stages per segment = tile halo along x and y
+constexpr int kHX = 4;   // tile origin: 4 columns left of the output window's first column - 1 (even: aligned pairs)
 #ifndef SPIN_RK5_TY
-#define SPIN_RK5_TY 24
+#define SPIN_RK5_TY 20
 #endif
 constexpr int kTY = SPIN_RK5_TY;   // thread rows = tile rows (one row per thread)
 constexpr int kNT = kPT * kTY;
-constexpr int kOutX = kPC - 2 * kHX, kOutY = kTY - 2 * kH;
+constexpr int kOutX = kPC - 2 * kH, kOutY = kTY - 2 * kH;   // output window: tile columns [kH, kH + kOutX)
 constexpr int kRec = 12;           // floats per site record of the carried vectors
 constexpr int kRowBytes = kPC * kRec * 4;              // one tile row of records
 constexpr int kSlotBytes = kTY * kRowBytes;            // one plane of the tile (B's ring slot)
@@ -275,7 +278,7 @@ __device__ __forceinline__ void r5_iteration(const Rk5Args& a, R5Rings& r, float
                 if (ry >= 0 && ry < kOutY) {
 #pragma unroll
                     for (int e = 0; e < 2; ++e) {
-                        const int ox = 2 * th.tx + e - kHX;
+                        const int ox = 2 * th.tx + e - kH;
                         if (ox < 0 || ox >= kOutX) continue;
                         float4* dst = reinterpret_cast<float4*>(ob + (ry * kOutX + ox) * kRec);
                         dst[0] = make_float4(pick(x4[0], e), pick(x4[1], e), pick(x4[2], e), pick(p5[0], e));
@@ -286,14 +289,16 @@ __device__ __forceinline__ void r5_iteration(const Rk5Args& a, R5Rings& r, float
                 fence_proxy_async();
                 __syncwarp();
                 if (th.tx == 0 && ry >= 0 && ry < kOutY) {
-                    // the row's output sites: columns bx*24 .. (no wrap; the
-                    // last tile may stop at the lattice edge)
+                    // the row's output sites: columns 26 bx - 1 .. 26 bx + 24
+                    // clipped to the lattice (no wrap: the first tile starts
+                    // at column 0, the last may stop at the lattice edge)
                     const int gy_u = (int)blockIdx.y * kOutY + ry;
-                    const int x0 = (int)blockIdx.x * kOutX;
-                    const int n = min(kOutX, a.nx - x0);
+                    const int xw = (int)blockIdx.x * kOutX - kHX + kH;
+                    const int off = xw < 0 ? -xw : 0;
+                    const int n = min(kOutX - off, a.nx - (xw + off));
                     if (gy_u < a.ny && n > 0) {
-                        bulk_s2g(a.car + (size_t)kRec * (unsigned)(t * th.plane + gy_u * a.nx + x0),
-                                 ob + ry * kOutX * kRec, (unsigned)(n * kRec * 4));
+                        bulk_s2g(a.car + (size_t)kRec * (unsigned)(t * th.plane + gy_u * a.nx + xw + off),
+                                 ob + (ry * kOutX + off) * kRec, (unsigned)(n * kRec * 4));
                         bulk_commit();
                     }
                 }
@@ -340,9 +345,10 @@ __device__ __forceinline__ void r5_iteration(const Rk5Args& a, R5Rings& r, float
                     oz = mul2(oz, inv);
                 }
                 const int base = t * th.plane;
-                if (a.pair8) {
-                    // both columns of a pair are outputs or neither (even row
-                    // length, even tile offsets): one 8-byte store per component
+                if (a.pair8 && th.out[0] == th.out[1]) {
+                    // both columns of the pair are outputs (or neither): one
+                    // 8-byte store per component; the pairs at the window's
+                    // edges (tile columns 2-3 and 28-29) store per site
                     if (th.out[0]) {
                         const int site = base + th.col[0];
                         *reinterpret_cast<f2*>(a.out0 + site) = ox;
@@ -388,7 +394,8 @@ __global__ void __launch_bounds__(kNT, 1) k_step_rk5(Rk5Args a) {
             const int cx = 2 * th.tx + e;
             const int gxu = (int)blockIdx.x * kOutX - kHX + cx;
             th.col[e] = gy * a.nx + wrapi(gxu, a.nx);
-            th.out[e] = cx >= kHX && cx < kPC - kHX && cy >= kH && cy < kTY - kH && gxu < a.nx && gyu < a.ny;
+            th.out[e] = cx >= kH && cx < kH + kOutX && cy >= kH && cy < kTY - kH && gxu >= 0 && gxu < a.nx &&
+                        gyu < a.ny;
             const float in = (gxu >= 0 && gxu < a.nx && gyu >= 0 && gyu < a.ny) ? 1.f : 0.f;
             if (e == 0) th.cmask.x = a.bc ? in : 1.f;
             else th.cmask.y = a.bc ? in : 1.f;
@@ -551,7 +558,8 @@ cudaError_t launch_step_rk5(const StepLaunch<float>& L) {
     a.out0 = L.out[0];
     a.out1 = L.out[1];
     a.out2 = L.out[2];
-    const int tiles_x = (L.g.nx + kOutX - 1) / kOutX;
+    // tile bx outputs columns kOutX bx - 1 .. kOutX bx + kOutX - 2
+    const int tiles_x = (L.g.nx + (kHX - kH) + kOutX - 1) / kOutX;
     const int tiles_y = (L.g.ny + kOutY - 1) / kOutY;
     // z chunks: one resident CTA per SM; minimise waves x (chunk planes +
     // pipeline fill of 2 x 3 - 2 iterations)

@@ -72,6 +72,9 @@ CASES = [
     ((1, 1, 1), 32, 1, 0, False, 0),
     ((64, 30, 21), 32, 1, 1, False, 0),
     ((128, 10, 7), 32, 1, 0, False, 0),
+    # rows of 26 and 52 columns: the last tile along x outputs one column
+    ((26, 9, 5), 32, 1, 1, False, 0),
+    ((52, 7, 6), 32, 1, 0, False, 0),
     ((20, 19, 18), 32, 1, 1, False, 1),
 ]
 
