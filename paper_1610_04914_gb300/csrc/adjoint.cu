@@ -190,7 +190,9 @@ struct StageIn {
 // Stage transpose, site-local part ("w-part") at a site for the stage with
 // input x and v = dt lam_K: w and u, the per-site field gradient gh += w (FP64)
 // and the site's terms <w, sum_nn x> (J) and 2 x_z w_z (D) added in FP64 to
-// the site's entries of gjd (J at i, D at N + i).
+// the site's entries of gjd (J at i, D at N + i).  (One FP64 add per term and
+// site: on this GPU's narrow FP64 pipe a per-block tree reduction, at five
+// adds per warp and value, measured slower.)
 // Every load of the site is issued before the arithmetic.
 template <typename real, bool PREC, bool HSITE>
 __device__ __forceinline__ void w_part(const StageIn<real>& in, const CV3<real>& hs, const Site<real>& st,
@@ -247,7 +249,9 @@ __device__ __forceinline__ void w_part(const StageIn<real>& in, const CV3<real>&
 }
 
 // Top of the transposed step: pulse and renormalisation transposes, lam_s =
-// lam_y, lam_K_j = b_j lam_y (stored for j < S-1), then the w-part of the
+// lam_y, lam_K_j = b_j lam_y (stored for j < S-1; for chain tableaus lam_y
+// itself is stored instead, since there lam_K_j = b_j lam_y + a_{j+1,j} lx_{j+1}
+// is formed where it is used), then the w-part of the
 // last stage S-1, whose lam_K is not changed by any other stage.
 template <typename real>
 struct TopArgs {
@@ -256,6 +260,7 @@ struct TopArgs {
     CV3<real> ystored;   // the unnormalised RK result, when the step stored it (c[0] null otherwise)
     LinComb<real> yc;    // otherwise y = s + sum_j b_j K_j (3N arrays)
     V3<real> LK[6];
+    V3<real> ly;         // chain tableaus: lam_y
     real b[6];
     int renorm, pulse;
     uint64_t seed, replica;
@@ -268,7 +273,7 @@ struct TopArgs {
     double* gjd;         // FP64 per-site dL/dJ (N) and dL/dD (N) terms
 };
 
-template <typename real, bool PREC, bool HSITE, int S>
+template <typename real, bool PREC, bool HSITE, int S, bool CHAIN>
 __global__ void __launch_bounds__(kAT) k_adj_top_w(TopArgs<real> a, AdjGeom<real> G) {
     const Site<real> st = site_here<real>(G.nx, G.ny, G.nz, G.bc);
     const int i = st.i;
@@ -301,11 +306,17 @@ __global__ void __launch_bounds__(kAT) k_adj_top_w(TopArgs<real> a, AdjGeom<real
         a.lam.c[0][i] = l0;
         a.lam.c[1][i] = l1;
         a.lam.c[2][i] = l2;
+        if (CHAIN) {
+            a.ly.c[0][i] = l0;
+            a.ly.c[1][i] = l1;
+            a.ly.c[2][i] = l2;
+        } else {
 #pragma unroll
-        for (int j = 0; j < S - 1; ++j) {
-            a.LK[j].c[0][i] = a.b[j] * l0;
-            a.LK[j].c[1][i] = a.b[j] * l1;
-            a.LK[j].c[2][i] = a.b[j] * l2;
+            for (int j = 0; j < S - 1; ++j) {
+                a.LK[j].c[0][i] = a.b[j] * l0;
+                a.LK[j].c[1][i] = a.b[j] * l1;
+                a.LK[j].c[2][i] = a.b[j] * l2;
+            }
         }
     }
     const real bl = a.b[S - 1] * G.dt;
@@ -316,15 +327,18 @@ __global__ void __launch_bounds__(kAT) k_adj_top_w(TopArgs<real> a, AdjGeom<real
 // Stage j of the transposed step: the neighbour part ("x-part") of stage j,
 // lx = u_j + J sum_nn w_j + 2D w_jz z, lam_s += lx, lam_K_l += a_jl lx (l < j),
 // and then (W) the w-part of stage j-1, which needs lam_K_{j-1} only at the
-// same site and is final once stage j's x-part has added to it.  w and u of
-// stage j are read from one buffer pair, those of stage j-1 written to the
-// other.
+// same site and is final once stage j's x-part has added to it.  For chain
+// tableaus lam_K_{j-1} = b_{j-1} lam_y + a_{j,j-1} lx is formed here from
+// lam_y (no lam_K arrays).  w and u of stage j are read from one buffer pair,
+// those of stage j-1 written to the other.
 template <typename real>
 struct XWArgs {
     CV3<real> w, u;      // stage j
     V3<real> lam;
     V3<real> LK[6];
+    CV3<real> ly;        // chain tableaus: lam_y
     real a[6];           // a_jl
+    real bl;             // chain tableaus: b_{j-1}
     StageIn<real> prev;  // input of stage j-1 and its neighbour sum
     CV3<real> hs;
     V3<real> wn, un;     // w, u of stage j-1
@@ -332,18 +346,23 @@ struct XWArgs {
     double* gjd;         // FP64 per-site dL/dJ (N) and dL/dD (N) terms
 };
 
-template <typename real, bool PREC, bool HSITE, int NL, bool W>
+template <typename real, bool PREC, bool HSITE, int NL, bool W, bool CHAIN>
 __global__ void __launch_bounds__(kAT) k_adj_xw(XWArgs<real> a, AdjGeom<real> G) {
     const Site<real> st = site_here<real>(G.nx, G.ny, G.nz, G.bc);
     const int i = st.i;
-    real ux[3], lm[3], wz, nsum[3], lkv[NL > 0 ? NL : 1][3];
+    constexpr int NLOAD = CHAIN ? 1 : (NL > 0 ? NL : 1);
+    real ux[3], lm[3], wz, nsum[3], lkv[NLOAD][3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         ux[c] = a.u.c[c][i];
         lm[c] = a.lam.c[c][i];
         nsum[c] = nbsum<real>(a.w.c[c], st);
+        if (CHAIN) {
+            if (NL > 0) lkv[0][c] = a.ly.c[c][i];
+        } else {
 #pragma unroll
-        for (int l = 0; l < NL; ++l) lkv[l][c] = a.LK[l].c[c][i];
+            for (int l = 0; l < NL; ++l) lkv[l][c] = a.LK[l].c[c][i];
+        }
     }
     wz = a.w.c[2][i];
     real lk[3] = {0, 0, 0};   // lam_K_{j-1} at the site after this stage
@@ -352,14 +371,21 @@ __global__ void __launch_bounds__(kAT) k_adj_xw(XWArgs<real> a, AdjGeom<real> G)
         real lx = ux[c] + G.J * nsum[c];
         if (c == 2) lx += G.twoD * wz;
         if (st.valid) a.lam.c[c][i] = lm[c] + lx;
+        if (CHAIN) {
+            if (NL > 0) {
+                const real base = a.bl * lkv[0][c];
+                lk[c] = base + a.a[NL - 1] * lx;
+            }
+        } else {
 #pragma unroll
-        for (int l = 0; l < NL; ++l) {
-            if (a.a[l] != real(0)) {
-                const real nv = lkv[l][c] + a.a[l] * lx;
-                if (st.valid) a.LK[l].c[c][i] = nv;
-                if (l == NL - 1) lk[c] = nv;
-            } else if (l == NL - 1) {
-                lk[c] = lkv[l][c];
+            for (int l = 0; l < NL; ++l) {
+                if (a.a[l] != real(0)) {
+                    const real nv = lkv[l][c] + a.a[l] * lx;
+                    if (st.valid) a.LK[l].c[c][i] = nv;
+                    if (l == NL - 1) lk[c] = nv;
+                } else if (l == NL - 1) {
+                    lk[c] = lkv[l][c];
+                }
             }
         }
     }
@@ -369,26 +395,31 @@ __global__ void __launch_bounds__(kAT) k_adj_xw(XWArgs<real> a, AdjGeom<real> G)
     }
 }
 
-// acc[q] += sum over sites of gjd[q N + i] (q = 0: J, 1: D), one block per
-// gradient, fixed order (deterministic).
-__global__ void k_adj_sum_jd(const double* __restrict__ gjd, long long N, double* __restrict__ acc) {
+// FP64 sums of kSumParts consecutive parts of each of the arrays at v + c N
+// (c < gridDim.y, N doubles each): block (p, c) writes parts[c kSumParts + p];
+// fixed order (deterministic).
+constexpr int kSumParts = 152;
+__global__ void k_adj_sum_parts(const double* __restrict__ v, long long N, double* __restrict__ parts) {
     __shared__ double red[kAW];
-    const double* g = gjd + (long long)blockIdx.x * N;
-    double v = 0;
-    for (long long q = threadIdx.x; q < N; q += blockDim.x) v += g[q];
-    const double t = block_sum<double>(v, red);
-    if (threadIdx.x == 0) acc[blockIdx.x] += t;
+    const long long c = blockIdx.y, p = blockIdx.x;
+    const long long lo = p * N / kSumParts, hi = (p + 1) * N / kSumParts;
+    const double* g = v + c * N;
+    double t = 0;
+    for (long long q = lo + threadIdx.x; q < hi; q += blockDim.x) t += g[q];
+    t = block_sum<double>(t, red);
+    if (threadIdx.x == 0) parts[c * kSumParts + p] = t;
 }
 
-// dL/dH = sum_i dL/dh_i: FP64 sums of the three components of the field
-// gradient, one block per component, fixed order.
-__global__ void k_adj_sum_gh(const double* __restrict__ gh, long long N, double* __restrict__ acc) {
+// acc[first + c] (+)= the FP64 sum of parts[c kSumParts ...] (one block per
+// array, fixed order): dL/dJ, dL/dD (added to the seed's explicit terms) from
+// the per-site terms, dL/dH = sum_i dL/dh_i from the field gradient.
+__global__ void k_adj_sum_final(const double* __restrict__ parts, double* __restrict__ acc, int first, int add) {
     __shared__ double red[kAW];
-    const double* g = gh + (long long)blockIdx.x * N;
+    const double* g = parts + (long long)blockIdx.x * kSumParts;
     double v = 0;
-    for (long long q = threadIdx.x; q < N; q += blockDim.x) v += g[q];
+    for (int q = threadIdx.x; q < kSumParts; q += blockDim.x) v += g[q];
     const double t = block_sum<double>(v, red);
-    if (threadIdx.x == 0) acc[2 + blockIdx.x] = t;
+    if (threadIdx.x == 0) acc[first + blockIdx.x] = add ? acc[first + blockIdx.x] + t : t;
 }
 
 // Loss seed: lam_i = (-dLdE H_eff,i + dLdM)/N from the final state, with the
@@ -480,10 +511,11 @@ size_t adjoint_workspace_bytes(const Geom& g, int elt, const Tableau& tb, int pa
     if (adjoint_stores_stages(g, elt, tb, path, K))
         b += al(comp) * (size_t)(2 * stages) * (size_t)K;   // X_j, sum_nn X_j and y of every step of a segment
     b += al(comp) * (size_t)(K + 1);     // segment states
-    b += al(comp) * (size_t)stages * 3;  // X_j, K_j, lam_K_j
+    b += al(comp) * (size_t)stages * 3;  // X_j, K_j, lam_K_j (lam_y in the first for chain tableaus)
     b += al(comp) * 6;                   // y, lam, w and u (two pairs)
     b += al(sizeof(double) * 3 * (size_t)g.N());   // FP64 field gradient when the caller does not want it
     b += al(sizeof(double) * 2 * (size_t)g.N());   // FP64 per-site dL/dJ and dL/dD terms
+    b += al(sizeof(double) * 5 * (size_t)kSumParts);           // per-part sums of those and of the field gradient
     b += al(sizeof(double) * 2 * (size_t)adjoint_blocks(g));   // the seed's per-block partials
     b += al(sizeof(double) * 8);         // accumulators
     b += al(sizeof(long long));          // pulse-number slot
@@ -504,47 +536,67 @@ void launch_lincomb(int nk, real* out, const real* s, const LinComb<real>& lc, l
     }
 }
 
+// The tableaus of the library: chain tableaus (RK4, RK2 midpoint, Heun) have
+// 2 or 4 stages, Butcher's RK5 (6 stages) is not a chain.
+inline bool adj_tableau_supported(int S, bool chain) { return chain ? (S == 2 || S == 4) : S == 6; }
+
 template <typename real, bool PREC, bool HSITE>
-void launch_xw_t(int j, const XWArgs<real>& a, const AdjGeom<real>& G, dim3 gb, cudaStream_t st) {
-    switch (j) {
-        case 0: k_adj_xw<real, PREC, HSITE, 0, false><<<gb, kAT, 0, st>>>(a, G); break;
-        case 1: k_adj_xw<real, PREC, HSITE, 1, true><<<gb, kAT, 0, st>>>(a, G); break;
-        case 2: k_adj_xw<real, PREC, HSITE, 2, true><<<gb, kAT, 0, st>>>(a, G); break;
-        case 3: k_adj_xw<real, PREC, HSITE, 3, true><<<gb, kAT, 0, st>>>(a, G); break;
-        case 4: k_adj_xw<real, PREC, HSITE, 4, true><<<gb, kAT, 0, st>>>(a, G); break;
-        default: k_adj_xw<real, PREC, HSITE, 5, true><<<gb, kAT, 0, st>>>(a, G); break;
+cudaError_t launch_xw_t(int j, int S, bool chain, const XWArgs<real>& a, const AdjGeom<real>& G, dim3 gb,
+                        cudaStream_t st) {
+    if (!adj_tableau_supported(S, chain)) return cudaErrorInvalidValue;
+    if (chain) {
+        switch (j) {
+            case 0: k_adj_xw<real, PREC, HSITE, 0, false, true><<<gb, kAT, 0, st>>>(a, G); break;
+            case 1: k_adj_xw<real, PREC, HSITE, 1, true, true><<<gb, kAT, 0, st>>>(a, G); break;
+            case 2: k_adj_xw<real, PREC, HSITE, 2, true, true><<<gb, kAT, 0, st>>>(a, G); break;
+            case 3: k_adj_xw<real, PREC, HSITE, 3, true, true><<<gb, kAT, 0, st>>>(a, G); break;
+            default: return cudaErrorInvalidValue;
+        }
+        return cudaSuccess;
     }
+    switch (j) {
+        case 0: k_adj_xw<real, PREC, HSITE, 0, false, false><<<gb, kAT, 0, st>>>(a, G); break;
+        case 1: k_adj_xw<real, PREC, HSITE, 1, true, false><<<gb, kAT, 0, st>>>(a, G); break;
+        case 2: k_adj_xw<real, PREC, HSITE, 2, true, false><<<gb, kAT, 0, st>>>(a, G); break;
+        case 3: k_adj_xw<real, PREC, HSITE, 3, true, false><<<gb, kAT, 0, st>>>(a, G); break;
+        case 4: k_adj_xw<real, PREC, HSITE, 4, true, false><<<gb, kAT, 0, st>>>(a, G); break;
+        case 5: k_adj_xw<real, PREC, HSITE, 5, true, false><<<gb, kAT, 0, st>>>(a, G); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaSuccess;
 }
 
 // x-part of stage j and (j > 0) w-part of stage j-1.
 template <typename real>
-void launch_xw(bool prec, bool hsite, int j, const XWArgs<real>& a, const AdjGeom<real>& G, dim3 gb, cudaStream_t st) {
+cudaError_t launch_xw(bool prec, bool hsite, int j, int S, bool chain, const XWArgs<real>& a, const AdjGeom<real>& G,
+                      dim3 gb, cudaStream_t st) {
     if (prec) {
-        if (hsite) launch_xw_t<real, true, true>(j, a, G, gb, st);
-        else launch_xw_t<real, true, false>(j, a, G, gb, st);
-    } else {
-        if (hsite) launch_xw_t<real, false, true>(j, a, G, gb, st);
-        else launch_xw_t<real, false, false>(j, a, G, gb, st);
+        if (hsite) return launch_xw_t<real, true, true>(j, S, chain, a, G, gb, st);
+        return launch_xw_t<real, true, false>(j, S, chain, a, G, gb, st);
     }
+    if (hsite) return launch_xw_t<real, false, true>(j, S, chain, a, G, gb, st);
+    return launch_xw_t<real, false, false>(j, S, chain, a, G, gb, st);
 }
 
 template <typename real, bool PREC, bool HSITE>
-void launch_top_w_t(int S, const TopArgs<real>& a, const AdjGeom<real>& G, dim3 gb, cudaStream_t st) {
-    if (S == 2) k_adj_top_w<real, PREC, HSITE, 2><<<gb, kAT, 0, st>>>(a, G);
-    else if (S == 4) k_adj_top_w<real, PREC, HSITE, 4><<<gb, kAT, 0, st>>>(a, G);
-    else k_adj_top_w<real, PREC, HSITE, 6><<<gb, kAT, 0, st>>>(a, G);
+cudaError_t launch_top_w_t(int S, bool chain, const TopArgs<real>& a, const AdjGeom<real>& G, dim3 gb,
+                           cudaStream_t st) {
+    if (chain && S == 2) k_adj_top_w<real, PREC, HSITE, 2, true><<<gb, kAT, 0, st>>>(a, G);
+    else if (chain && S == 4) k_adj_top_w<real, PREC, HSITE, 4, true><<<gb, kAT, 0, st>>>(a, G);
+    else if (!chain && S == 6) k_adj_top_w<real, PREC, HSITE, 6, false><<<gb, kAT, 0, st>>>(a, G);
+    else return cudaErrorInvalidValue;
+    return cudaSuccess;
 }
 
 template <typename real>
-void launch_top_w(bool prec, bool hsite, int S, const TopArgs<real>& a, const AdjGeom<real>& G, dim3 gb,
-                  cudaStream_t st) {
+cudaError_t launch_top_w(bool prec, bool hsite, int S, bool chain, const TopArgs<real>& a, const AdjGeom<real>& G,
+                         dim3 gb, cudaStream_t st) {
     if (prec) {
-        if (hsite) launch_top_w_t<real, true, true>(S, a, G, gb, st);
-        else launch_top_w_t<real, true, false>(S, a, G, gb, st);
-    } else {
-        if (hsite) launch_top_w_t<real, false, true>(S, a, G, gb, st);
-        else launch_top_w_t<real, false, false>(S, a, G, gb, st);
+        if (hsite) return launch_top_w_t<real, true, true>(S, chain, a, G, gb, st);
+        return launch_top_w_t<real, true, false>(S, chain, a, G, gb, st);
     }
+    if (hsite) return launch_top_w_t<real, false, true>(S, chain, a, G, gb, st);
+    return launch_top_w_t<real, false, false>(S, chain, a, G, gb, st);
 }
 
 template <typename real>
@@ -590,6 +642,7 @@ cudaError_t adjoint_run(const AdjointRun<real>& A) {
     off += al(compb);   // (unused slot, kept so the layout matches adjoint_workspace_bytes)
     real* lam = reinterpret_cast<real*>(ws + off);
     off += al(compb);
+    if (!adj_tableau_supported(S, tb.chain)) return cudaErrorInvalidValue;
     real* wb[2];   // w and u of the stages, double-buffered by stage parity
     real* ub[2];
     for (int q = 0; q < 2; ++q) {
@@ -606,6 +659,8 @@ cudaError_t adjoint_run(const AdjointRun<real>& A) {
     const dim3 gb = grid3(g);
     double* gjd = reinterpret_cast<double*>(ws + off);
     off += al(sizeof(double) * 2 * (size_t)N);
+    double* parts = reinterpret_cast<double*>(ws + off);
+    off += al(sizeof(double) * 5 * (size_t)kSumParts);
     double* partials = reinterpret_cast<double*>(ws + off);
     off += al(sizeof(double) * 2 * (size_t)nb);
     double* acc = reinterpret_cast<double*>(ws + off);
@@ -741,6 +796,7 @@ cudaError_t adjoint_run(const AdjointRun<real>& A) {
                 ta.LK[j] = v3<real>(LK[j], N);
                 ta.b[j] = (real)tb.b[j];
             }
+            ta.ly = v3<real>(LK[0], N);   // chain tableaus: lam_y in the first lam_K buffer
             ta.renorm = A.renorm;
             ta.pulse = pul ? 1 : 0;
             ta.seed = A.seed;
@@ -753,7 +809,7 @@ cudaError_t adjoint_run(const AdjointRun<real>& A) {
             ta.u = v3<real>(ub[(S - 1) & 1], N);
             ta.gh = gh3;
             ta.gjd = gjd;
-            launch_top_w<real>(A.precession != 0, HS, S, ta, G, gb, st);
+            if ((e = launch_top_w<real>(A.precession != 0, HS, S, tb.chain, ta, G, gb, st)) != cudaSuccess) return e;
             for (int j = S - 1; j >= 0; --j) {
                 XWArgs<real> xa{};
                 xa.w = cv3<real>(wb[j & 1], N);
@@ -763,6 +819,8 @@ cudaError_t adjoint_run(const AdjointRun<real>& A) {
                     xa.LK[l] = v3<real>(LK[l], N);
                     xa.a[l] = (real)tb.a[j][l];
                 }
+                xa.ly = cv3<real>(LK[0], N);
+                xa.bl = j > 0 ? (real)tb.b[j - 1] : real(0);
                 if (j > 0) {
                     xa.prev = in[j - 1];
                     xa.wn = v3<real>(wb[(j - 1) & 1], N);
@@ -771,13 +829,18 @@ cudaError_t adjoint_run(const AdjointRun<real>& A) {
                 xa.hs = hs3;
                 xa.gh = gh3;
                 xa.gjd = gjd;
-                launch_xw<real>(A.precession != 0, HS, j, xa, G, gb, st);
+                if ((e = launch_xw<real>(A.precession != 0, HS, j, S, tb.chain, xa, G, gb, st)) != cudaSuccess)
+                    return e;
             }
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
     }
-    k_adj_sum_jd<<<2, kAT, 0, st>>>(gjd, N, acc);
-    k_adj_sum_gh<<<3, kAT, 0, st>>>(gh, N, acc);
+    // dL/dJ, dL/dD (added to the seed's explicit terms) and dL/dH: FP64 sums in
+    // two deterministic passes
+    k_adj_sum_parts<<<dim3(kSumParts, 2), kAT, 0, st>>>(gjd, N, parts);
+    k_adj_sum_parts<<<dim3(kSumParts, 3), kAT, 0, st>>>(gh, N, parts + 2 * kSumParts);
+    k_adj_sum_final<<<2, kAT, 0, st>>>(parts, acc, 0, 1);
+    k_adj_sum_final<<<3, kAT, 0, st>>>(parts + 2 * kSumParts, acc, 2, 0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // results: gradient accumulators to the host, dL/ds_0 to the caller
     if (A.g_s0) {
