@@ -44,6 +44,11 @@ RK4_FLOPS_PER_SPIN_STEP = 240.0
 # 6 right-hand sides x 29, 5 non-zero weights x 3 FMA, renormalisation 9
 RK5_FLOPS_PER_SINGLE_STEP = 285.0
 BYTES_PER_SPIN_STEP_FP32 = 24.0
+# algorithmic bytes of one backward spin-step of the checkpointed adjoint
+# (FP32 state, FP64 field gradient): the recomputed forward step (state read +
+# write, 24), the step's input state read by the transposes (12), the adjoint
+# state read + write (24), the FP64 dL/dh_i read + write (48)
+ADJ_BYTES_PER_SPIN_STEP = 108.0
 
 
 def _dist():
@@ -773,6 +778,13 @@ def run_ours(args, ws, rank, local):
     if adj is not None:
         adj.pop("_gh")
         adj["vs_fp64"] = adjoint_vs_fp64(sp, torch, dev, adj)
+        n_adj = int(np.prod(spin_inputs.WORKLOADS["adjoint64"]["n"]))
+        hbm_pk, pk_src = _measured_peaks()
+        ach = ADJ_BYTES_PER_SPIN_STEP * n_adj / (adj["adjoint_ms_per_step"] * 1e-3) / 1e9
+        adj["roofline"] = {"bound": "hbm", "achieved": ach, "peak": hbm_pk, "unit": "GB/s", "frac": ach / hbm_pk,
+                           "bytes_per_spin_step": ADJ_BYTES_PER_SPIN_STEP, "traffic": None,
+                           "peak_source": f"{pk_src} HBM copy bandwidth",
+                           "note": "whole backward pass per step (recompute + transposes) by wall clock"}
     bat = batch_timing(sp, torch, dev, flush, stream, hbm_peak) if rank == 0 and not args.no_extra else None
     k256 = kernel_timing_256(sp, torch, dev, flush, stream, hbm_peak) if rank == 0 and not args.no_extra else None
     f64 = fp64_step_timing(sp, torch, dev, flush, stream) if rank == 0 and not args.no_extra else None
@@ -854,7 +866,7 @@ def _escape_replicas(sp, nrep, precision):
 def run_profile_case(args):
     """A small fixed case for ncu: the benchmark's physics on an L^3 FP32
     lattice, advanced by single eager steps (step 5 of each interval carries
-    the pulse)."""
+    the pulse); --profile-integrator rk5 runs Butcher RK5 instead of RK4."""
     import torch
 
     import paper_1610_04914_gb300 as sp
@@ -865,6 +877,9 @@ def run_profile_case(args):
     L = args.profile_lattice
     w["n"] = (L, L, L)
     p = _params(sp, w, 0)
+    if args.profile_integrator == "rk5":
+        import dataclasses
+        p = dataclasses.replace(p, integrator=sp.RK5_BUTCHER)
     s0 = spin_inputs.random_spins(L, L, L, seed=w["spin_seed"])
     lat = sp.Lattice(p, torch.from_numpy(s0), device="cuda:0")
     for _ in range(args.profile_steps):
@@ -961,6 +976,8 @@ def main():
     ap.add_argument("--profile-lattice", type=int, default=0,
                     help="profiling driver: L^3 FP32 RK4 lattice, --profile-steps single steps, no timing")
     ap.add_argument("--profile-steps", type=int, default=4)
+    ap.add_argument("--profile-integrator", default="rk4", choices=["rk4", "rk5"],
+                    help="integrator of --profile-lattice")
     ap.add_argument("--profile-adjoint", action="store_true",
                     help="profiling driver: 64^3 adjoint workload with --profile-steps steps")
     ap.add_argument("--profile-mc", type=int, default=0,
