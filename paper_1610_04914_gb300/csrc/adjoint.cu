@@ -273,11 +273,11 @@ struct TopArgs {
     double* gjd;         // FP64 per-site dL/dJ (N) and dL/dD (N) terms
 };
 
+// The top at a site, given the adjoint (l0, l1, l2) of the step's output.
 template <typename real, bool PREC, bool HSITE, int S, bool CHAIN>
-__global__ void __launch_bounds__(kAT) k_adj_top_w(TopArgs<real> a, AdjGeom<real> G) {
-    const Site<real> st = site_here<real>(G.nx, G.ny, G.nz, G.bc);
+__device__ __forceinline__ void top_body(const TopArgs<real>& a, const AdjGeom<real>& G, const Site<real>& st, real l0,
+                                         real l1, real l2) {
     const int i = st.i;
-    real l0 = a.lam.c[0][i], l1 = a.lam.c[1][i], l2 = a.lam.c[2][i];
     if (a.pulse) {
         const Words4 wd = noise_words(a.seed, (uint64_t)i, (uint64_t)a.k, a.replica);
         real g0, g1, g2;
@@ -322,6 +322,13 @@ __global__ void __launch_bounds__(kAT) k_adj_top_w(TopArgs<real> a, AdjGeom<real
     const real bl = a.b[S - 1] * G.dt;
     const real v[3] = {bl * l0, bl * l1, bl * l2};
     w_part<real, PREC, HSITE>(a.last, a.hs, st, G, v, a.w, a.u, a.gh, a.gjd);
+}
+
+template <typename real, bool PREC, bool HSITE, int S, bool CHAIN>
+__global__ void __launch_bounds__(kAT) k_adj_top_w(TopArgs<real> a, AdjGeom<real> G) {
+    const Site<real> st = site_here<real>(G.nx, G.ny, G.nz, G.bc);
+    const int i = st.i;
+    top_body<real, PREC, HSITE, S, CHAIN>(a, G, st, a.lam.c[0][i], a.lam.c[1][i], a.lam.c[2][i]);
 }
 
 // Stage j of the transposed step: the neighbour part ("x-part") of stage j,
@@ -393,6 +400,33 @@ __global__ void __launch_bounds__(kAT) k_adj_xw(XWArgs<real> a, AdjGeom<real> G)
         const real v[3] = {G.dt * lk[0], G.dt * lk[1], G.dt * lk[2]};
         w_part<real, PREC, HSITE>(a.prev, a.hs, st, G, v, a.wn, a.un, a.gh, a.gjd);
     }
+}
+
+// The first stage's x-part of step m (lam_s += lx, final: the adjoint of step
+// m's input state) fused with the top of step m-1, which needs that adjoint
+// at the same site only: one launch and one read and write of lam fewer per
+// step.  For steps whose stages were stored (the top then reads only stored
+// arrays of step m-1).
+template <typename real, bool PREC, bool HSITE, int S, bool CHAIN>
+__global__ void __launch_bounds__(kAT) k_adj_x0_top(XWArgs<real> a, TopArgs<real> ta, AdjGeom<real> G) {
+    const Site<real> st = site_here<real>(G.nx, G.ny, G.nz, G.bc);
+    const int i = st.i;
+    real ux[3], lm[3], nsum[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        ux[c] = a.u.c[c][i];
+        lm[c] = a.lam.c[c][i];
+        nsum[c] = nbsum<real>(a.w.c[c], st);
+    }
+    const real wz = a.w.c[2][i];
+    real l[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        real lx = ux[c] + G.J * nsum[c];
+        if (c == 2) lx += G.twoD * wz;
+        l[c] = lm[c] + lx;
+    }
+    top_body<real, PREC, HSITE, S, CHAIN>(ta, G, st, l[0], l[1], l[2]);
 }
 
 // FP64 sums of kSumParts consecutive parts of each of the arrays at v + c N
@@ -579,6 +613,26 @@ cudaError_t launch_xw(bool prec, bool hsite, int j, int S, bool chain, const XWA
 }
 
 template <typename real, bool PREC, bool HSITE>
+cudaError_t launch_x0_top_t(int S, bool chain, const XWArgs<real>& xa, const TopArgs<real>& ta, const AdjGeom<real>& G,
+                            dim3 gb, cudaStream_t st) {
+    if (chain && S == 2) k_adj_x0_top<real, PREC, HSITE, 2, true><<<gb, kAT, 0, st>>>(xa, ta, G);
+    else if (chain && S == 4) k_adj_x0_top<real, PREC, HSITE, 4, true><<<gb, kAT, 0, st>>>(xa, ta, G);
+    else return cudaErrorInvalidValue;
+    return cudaSuccess;
+}
+
+template <typename real>
+cudaError_t launch_x0_top(bool prec, bool hsite, int S, bool chain, const XWArgs<real>& xa, const TopArgs<real>& ta,
+                          const AdjGeom<real>& G, dim3 gb, cudaStream_t st) {
+    if (prec) {
+        if (hsite) return launch_x0_top_t<real, true, true>(S, chain, xa, ta, G, gb, st);
+        return launch_x0_top_t<real, true, false>(S, chain, xa, ta, G, gb, st);
+    }
+    if (hsite) return launch_x0_top_t<real, false, true>(S, chain, xa, ta, G, gb, st);
+    return launch_x0_top_t<real, false, false>(S, chain, xa, ta, G, gb, st);
+}
+
+template <typename real, bool PREC, bool HSITE>
 cudaError_t launch_top_w_t(int S, bool chain, const TopArgs<real>& a, const AdjGeom<real>& G, dim3 gb,
                            cudaStream_t st) {
     if (chain && S == 2) k_adj_top_w<real, PREC, HSITE, 2, true><<<gb, kAT, 0, st>>>(a, G);
@@ -754,39 +808,22 @@ cudaError_t adjoint_run(const AdjointRun<real>& A) {
             e = launch_step<real>(L);
             if (e != cudaSuccess) return e;
         }
-        // transposed steps, last to first
-        for (int m = seglen; m >= 1; --m) {
-            const long long n = start + m;
-            const bool pul = A.noise && (n % A.R) == (A.R / 2);
+        // transposed steps, last to first.  With stored stages the first
+        // stage's x-part of step m and the top of step m-1 share a launch.
+        auto stage_inputs = [&](int m, StageIn<real>* in) {
             const real* s = seg + (size_t)(m - 1) * len;
-            // stages X_j and K_j = dt f(X_j) (recomputed when not stored); the
-            // first stage's input is s itself
-            StageIn<real> in[6];
+            // the first stage's input is s itself
             for (int j = 0; j < S; ++j) {
                 in[j].x = cv3<real>((j == 0) ? s : (stored ? stage_x(j + 1, m) : X[j]), N);
                 in[j].sn = cv3<real>(stored ? stage_sn(j + 1, m) : nullptr, N);
             }
-            for (int j = 0; j < S && !stored; ++j) {
-                if (j > 0) {
-                    LinComb<real> lc{};
-                    for (int l = 0; l < j; ++l) {
-                        lc.K[l] = Kst[l];
-                        lc.coef[l] = (real)tb.a[j][l];
-                    }
-                    launch_lincomb<real>(j, X[j], s, lc, len, st);
-                }
-                const V3<real> K3 = v3<real>(Kst[j], N);
-                if (A.precession) {
-                    if (HS) k_adj_rhs<real, true, true><<<gb, kAT, 0, st>>>(in[j].x, hs3, K3, G);
-                    else k_adj_rhs<real, true, false><<<gb, kAT, 0, st>>>(in[j].x, hs3, K3, G);
-                } else {
-                    if (HS) k_adj_rhs<real, false, true><<<gb, kAT, 0, st>>>(in[j].x, hs3, K3, G);
-                    else k_adj_rhs<real, false, false><<<gb, kAT, 0, st>>>(in[j].x, hs3, K3, G);
-                }
-            }
+        };
+        auto top_args = [&](int m, const StageIn<real>* in) {
+            const long long n = start + m;
+            const bool pul = A.noise && (n % A.R) == (A.R / 2);
             TopArgs<real> ta{};
             ta.lam = v3<real>(lam, N);
-            ta.s = s;
+            ta.s = seg + (size_t)(m - 1) * len;
             ta.ystored = cv3<real>(stored ? stage_y(m) : nullptr, N);
             for (int l = 0; l < S; ++l) {
                 ta.yc.K[l] = Kst[l];
@@ -809,28 +846,69 @@ cudaError_t adjoint_run(const AdjointRun<real>& A) {
             ta.u = v3<real>(ub[(S - 1) & 1], N);
             ta.gh = gh3;
             ta.gjd = gjd;
-            if ((e = launch_top_w<real>(A.precession != 0, HS, S, tb.chain, ta, G, gb, st)) != cudaSuccess) return e;
-            for (int j = S - 1; j >= 0; --j) {
-                XWArgs<real> xa{};
-                xa.w = cv3<real>(wb[j & 1], N);
-                xa.u = cv3<real>(ub[j & 1], N);
-                xa.lam = v3<real>(lam, N);
-                for (int l = 0; l < j; ++l) {
-                    xa.LK[l] = v3<real>(LK[l], N);
-                    xa.a[l] = (real)tb.a[j][l];
-                }
-                xa.ly = cv3<real>(LK[0], N);
-                xa.bl = j > 0 ? (real)tb.b[j - 1] : real(0);
+            return ta;
+        };
+        auto xw_args = [&](int j, const StageIn<real>* in) {
+            XWArgs<real> xa{};
+            xa.w = cv3<real>(wb[j & 1], N);
+            xa.u = cv3<real>(ub[j & 1], N);
+            xa.lam = v3<real>(lam, N);
+            for (int l = 0; l < j; ++l) {
+                xa.LK[l] = v3<real>(LK[l], N);
+                xa.a[l] = (real)tb.a[j][l];
+            }
+            xa.ly = cv3<real>(LK[0], N);
+            xa.bl = j > 0 ? (real)tb.b[j - 1] : real(0);
+            if (j > 0) {
+                xa.prev = in[j - 1];
+                xa.wn = v3<real>(wb[(j - 1) & 1], N);
+                xa.un = v3<real>(ub[(j - 1) & 1], N);
+            }
+            xa.hs = hs3;
+            xa.gh = gh3;
+            xa.gjd = gjd;
+            return xa;
+        };
+        const bool fuse_top = stored && tb.chain;
+        for (int m = seglen; m >= 1; --m) {
+            const real* s = seg + (size_t)(m - 1) * len;
+            StageIn<real> in[6];
+            stage_inputs(m, in);
+            // stages X_j and K_j = dt f(X_j), recomputed when not stored
+            for (int j = 0; j < S && !stored; ++j) {
                 if (j > 0) {
-                    xa.prev = in[j - 1];
-                    xa.wn = v3<real>(wb[(j - 1) & 1], N);
-                    xa.un = v3<real>(ub[(j - 1) & 1], N);
+                    LinComb<real> lc{};
+                    for (int l = 0; l < j; ++l) {
+                        lc.K[l] = Kst[l];
+                        lc.coef[l] = (real)tb.a[j][l];
+                    }
+                    launch_lincomb<real>(j, X[j], s, lc, len, st);
                 }
-                xa.hs = hs3;
-                xa.gh = gh3;
-                xa.gjd = gjd;
-                if ((e = launch_xw<real>(A.precession != 0, HS, j, S, tb.chain, xa, G, gb, st)) != cudaSuccess)
+                const V3<real> K3 = v3<real>(Kst[j], N);
+                if (A.precession) {
+                    if (HS) k_adj_rhs<real, true, true><<<gb, kAT, 0, st>>>(in[j].x, hs3, K3, G);
+                    else k_adj_rhs<real, true, false><<<gb, kAT, 0, st>>>(in[j].x, hs3, K3, G);
+                } else {
+                    if (HS) k_adj_rhs<real, false, true><<<gb, kAT, 0, st>>>(in[j].x, hs3, K3, G);
+                    else k_adj_rhs<real, false, false><<<gb, kAT, 0, st>>>(in[j].x, hs3, K3, G);
+                }
+            }
+            if (!fuse_top || m == seglen) {
+                const TopArgs<real> ta = top_args(m, in);
+                if ((e = launch_top_w<real>(A.precession != 0, HS, S, tb.chain, ta, G, gb, st)) != cudaSuccess)
                     return e;
+            }
+            for (int j = S - 1; j >= 0; --j) {
+                const XWArgs<real> xa = xw_args(j, in);
+                if (j == 0 && fuse_top && m > 1) {
+                    StageIn<real> inp[6];
+                    stage_inputs(m - 1, inp);
+                    const TopArgs<real> ta = top_args(m - 1, inp);
+                    if ((e = launch_x0_top<real>(A.precession != 0, HS, S, tb.chain, xa, ta, G, gb, st)) != cudaSuccess)
+                        return e;
+                } else if ((e = launch_xw<real>(A.precession != 0, HS, j, S, tb.chain, xa, G, gb, st)) != cudaSuccess) {
+                    return e;
+                }
             }
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
