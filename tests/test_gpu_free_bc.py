@@ -26,6 +26,9 @@ CASES = [  # size, precision, integrator, precession, h_site, path
     ((20, 19, 18), 32, 1, 1, False, 0),
     ((2, 3, 5), 32, 1, 0, False, 0),
     ((64, 19, 9), 32, 1, 1, False, 0),
+    # RK4 on shapes that qualify for TMA staging (sides multiples of 4, x >= 24, y >= 16)
+    ((24, 16, 9), 32, 0, 1, True, 0),
+    ((52, 36, 10), 32, 0, 0, False, 0),
 ]
 
 

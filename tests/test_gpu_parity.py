@@ -76,6 +76,12 @@ CASES = [
     ((26, 9, 5), 32, 1, 1, False, 0),
     ((52, 7, 6), 32, 1, 0, False, 0),
     ((20, 19, 18), 32, 1, 1, False, 1),
+    # RK4 on lattices whose x and y sides are multiples of 4 (x >= 24,
+    # y >= 16), the shapes that also qualify for TMA staging
+    ((24, 16, 9), 32, 0, 1, False, 0),
+    ((48, 40, 20), 32, 0, 1, True, 0),
+    ((128, 36, 17), 32, 0, 0, False, 0),
+    ((28, 20, 11), 32, 0, 1, True, 0),
 ]
 
 
@@ -185,6 +191,28 @@ def test_observables(gpu, orc, prec, shape):
     tm, te = (1e-13, 1e-13) if prec == 64 else (1e-6, 5e-6)
     assert np.max(np.abs(np.array(M) - ref[:3])) < tm
     assert abs(E - ref[3]) < te
+
+
+@pytest.mark.parametrize("shape,hsite,bc", [((48, 40, 20), False, 0), ((28, 20, 11), True, 1),
+                                             ((128, 36, 17), True, 0), ((72, 64, 33), False, 1)])
+def test_tma_staging_bitwise(gpu, shape, hsite, bc, monkeypatch):
+    """RK4 lattices that qualify for TMA staging (SPIN_TMA=1) give bitwise the
+    same states (20 steps, two pulses) as with the spin planes staged per
+    thread by cp.async (the default): the two stagings move the same values
+    into the tile and every output site keeps its arithmetic."""
+    nx, ny, nz = shape
+    p = gpu.Params(nx, ny, nz, J=1.0, D=0.05, H=(0.01, -0.02, 0.02), lam=0.05, T=1.0, dt=0.1, R=10, seed=3,
+                   precision=32, bc=bc)
+    s0 = spin_inputs.random_spins(nx, ny, nz, seed=2)
+    hs = spin_inputs.site_fields(nx, ny, nz, 0.1, seed=4) if hsite else None
+    monkeypatch.setenv("SPIN_TMA", "1")
+    a, la = run_gpu(gpu, p, s0, 20, h_site=hs)
+    monkeypatch.delenv("SPIN_TMA", raising=False)
+    b, lb = run_gpu(gpu, p, s0, 20, h_site=hs)
+    monkeypatch.delenv("SPIN_TMA", raising=False)
+    la.close()
+    lb.close()
+    assert np.array_equal(a, b)
 
 
 # ----------------------------------------------------------------- graph path, resume
