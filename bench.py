@@ -206,7 +206,8 @@ class ClockSampler:
 
 
 # the sources k_step_patch is compiled from (its own file and the headers it includes)
-PATCH_KERNEL_SOURCES = ("step_patch.cu", "patch_common.cuh", "spin_device.cuh", "spin_internal.h")
+PATCH_KERNEL_SOURCES = ("step_patch.cu", "patch_tile.cuh", "patch_tmem.cuh", "patch_common.cuh", "spin_device.cuh",
+                        "spin_internal.h")
 
 
 def _kernel_source_hash():
@@ -637,19 +638,33 @@ def mc_timing(sp, torch, stream, hbm_peak):
 
 def kernel_timing_256(sp, torch, dev, flush, stream, hbm_peak):
     """The same fused RK4 step on a 256^3 lattice (201 MB per state copy,
-    larger than L2): plain-step launch time and its HBM fraction."""
+    larger than L2): plain-step launch time and its HBM fraction.  At this
+    size the library picks the step with its older planes in tensor memory
+    (28-row tiles, no z chunks); the register-ring step (SPIN_TMEM=0) is
+    timed beside it."""
     w = dict(spin_inputs.WORKLOADS[WORKLOAD])
     w["n"] = (256, 256, 256)
     p = _params(sp, w, 0)
     s0 = spin_inputs.random_spins(256, 256, 256, seed=w["spin_seed"])
-    with torch.cuda.stream(stream):
-        lat = sp.Lattice(p, torch.from_numpy(s0), device=dev, stream=stream)
-        lat.step(p.R)
-    ms = float(np.mean(time_plain_steps(torch, lat, p.R, 2, stream, flush)))
-    lat.close()
+    out = {}
+    for label, env in (("tmem", None), ("register_rings", "0")):
+        if env is None:
+            os.environ.pop("SPIN_TMEM", None)
+        else:
+            os.environ["SPIN_TMEM"] = env
+        try:
+            with torch.cuda.stream(stream):
+                lat = sp.Lattice(p, torch.from_numpy(s0), device=dev, stream=stream)
+                lat.step(p.R)
+            out[label] = float(np.mean(time_plain_steps(torch, lat, p.R, 2, stream, flush)))
+            lat.close()
+        finally:
+            os.environ.pop("SPIN_TMEM", None)
+    ms = out["tmem"]
     gbs = BYTES_PER_SPIN_STEP_FP32 * p.N / (ms / 1e3) / 1e9
-    return {"lattice": "256^3", "kernel_ms_per_launch": ms, "achieved_GBps": gbs, "frac": gbs / hbm_peak,
-            "spin_steps_per_s": p.N / (ms / 1e3)}
+    return {"lattice": "256^3", "kernel": "k_step_patch_tmem<PREC=1> (s and y rings in tensor memory, 28-row tiles)",
+            "kernel_ms_per_launch": ms, "achieved_GBps": gbs, "frac": gbs / hbm_peak,
+            "spin_steps_per_s": p.N / (ms / 1e3), "register_rings_ms_per_launch": out["register_rings"]}
 
 
 def fp64_step_timing(sp, torch, dev, flush, stream):

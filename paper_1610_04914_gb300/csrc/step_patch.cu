@@ -21,6 +21,7 @@
 #include <cstdlib>
 
 #include "patch_tile.cuh"
+#include "patch_tmem.cuh"
 
 namespace spin {
 
@@ -52,6 +53,45 @@ __global__ void __launch_bounds__(kPT* PatchShape<S>::TY, 1)
     float* sh = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     patch_tile<S, PREC, HSITE, false, STORE, 0, true>(a, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z, sh,
                                                       &maps);
+}
+
+// RK4 step with the spin and accumulator rings of its older planes in tensor
+// memory and 28-row tiles (patch_tmem.cuh).
+template <bool PREC>
+__global__ void __launch_bounds__(kPT* PatchShape<4, kTmemVariant>::TY, 1) k_step_patch_tmem(PatchArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ unsigned tm_slot;
+    tm_tile<PREC>(a, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z, reinterpret_cast<float*>(smem_raw), &tm_slot);
+}
+
+template <bool PREC>
+cudaError_t patch_tmem_launch(const PatchArgs& a, dim3 grid, cudaStream_t st, bool prepare) {
+    const size_t smem = patch_smem<4, PREC, false, false, kTmemVariant>();
+    if (prepare)
+        return cudaFuncSetAttribute(k_step_patch_tmem<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_step_patch_tmem<PREC><<<grid, dim3(kPT, PatchShape<4, kTmemVariant>::TY), smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+// z chunks of a tiling: one resident CTA per SM, so the chunk length that
+// minimises waves x (chunk planes + pipeline fill of 2S-2 iterations); the
+// returned cost is that product
+int choose_chunk(int nz, long long tiles, int S, double* cost) {
+    int best_chunks = 1;
+    double best_cost = 1e300;
+    for (int c = 1; c <= std::max(1, nz / 4); ++c) {
+        const int zc_c = (nz + c - 1) / c;
+        const int used = (nz + zc_c - 1) / zc_c;
+        const long long ctas = tiles * used;
+        const double waves = (double)((ctas + 151) / 152);
+        const double cst = waves * (zc_c + 2 * S - 2);
+        if (cst < best_cost - 1e-9) {
+            best_cost = cst;
+            best_chunks = c;
+        }
+    }
+    if (cost) *cost = best_cost;
+    return (nz + best_chunks - 1) / best_chunks;
 }
 
 template <int S>
@@ -225,39 +265,46 @@ cudaError_t prepare_patch_kernels() {
     if (e != cudaSuccess) return e;
     e = patch_store_dispatch<2>(a, dim3(1), 0, false, false, true);
     if (e != cudaSuccess) return e;
+    if ((e = patch_tmem_launch<true>(a, dim3(1), 0, true)) != cudaSuccess) return e;
+    if ((e = patch_tmem_launch<false>(a, dim3(1), 0, true)) != cudaSuccess) return e;
     return patch_tma_dispatch<4>(a, nullptr, dim3(1), 0, false, false, false, true);
 }
 
 cudaError_t launch_step_patch(const StepLaunch<float>& L) {
     const int S = L.tab->stages;
     PatchArgs a = patch_args_common(L);
+    const bool hs = L.hs[0] != nullptr;
+    const bool store = L.st_n[0][0] != nullptr;
     const int outx = kPC - 2 * S;
-    const int outy = patch_out_y(S, 0);
     const int tiles_x = (L.g.nx + outx - 1) / outx;
+    // register-ring tiling (24 rows for RK4) ...
+    const int outy = patch_out_y(S, 0);
     const int tiles_y = (L.g.ny + outy - 1) / outy;
-    // z chunks: one resident CTA per SM, so pick the chunk count that
-    // minimises waves x (chunk planes + pipeline fill of 2S-2 iterations)
-    const long long tiles = (long long)tiles_x * tiles_y;
-    int best_chunks = 1;
-    double best_cost = 1e300;
-    for (int c = 1; c <= std::max(1, L.g.nz / 4); ++c) {
-        const int zc_c = (L.g.nz + c - 1) / c;
-        const int used = (L.g.nz + zc_c - 1) / zc_c;
-        const long long ctas = tiles * used;
-        const double waves = (double)((ctas + 151) / 152);
-        const double cost = waves * (zc_c + 2 * S - 2);
-        if (cost < best_cost - 1e-9) {
-            best_cost = cost;
-            best_chunks = c;
+    double cost = 0;
+    int zc = choose_chunk(L.g.nz, (long long)tiles_x * tiles_y, S, &cost);
+    dim3 grid(tiles_x, tiles_y, (L.g.nz + zc - 1) / zc);
+    // ... or, for a plain RK4 step staged by cp.async, the TMEM-ring tiling
+    // (28 rows) where its estimated time, waves x iterations x tile rows, is
+    // lower (SPIN_TMEM=0 / =1 in the environment forbids / forces it)
+    const bool use_tma = !store && tma_applies(a, S);
+    bool tmem = false;
+    if (S == 4 && !hs && !store && !use_tma) {
+        const char* env = std::getenv("SPIN_TMEM");
+        if (!env || env[0] != '0') {
+            constexpr int rows_r = PatchShape<4, 0>::TY, rows_t = PatchShape<4, kTmemVariant>::TY;
+            const int ty_t = (L.g.ny + (rows_t - 8) - 1) / (rows_t - 8);
+            double cost_t = 0;
+            const int zc_t = choose_chunk(L.g.nz, (long long)tiles_x * ty_t, S, &cost_t);
+            if ((env && env[0] == '1') || cost_t * rows_t < cost * rows_r) {
+                tmem = true;
+                zc = zc_t;
+                grid = dim3(tiles_x, ty_t, (L.g.nz + zc_t - 1) / zc_t);
+            }
         }
     }
-    const int zc = (L.g.nz + best_chunks - 1) / best_chunks;
     a.tz = zc;
     a.n_iter = zc + 2 * S - 2;
-    dim3 grid(tiles_x, tiles_y, (L.g.nz + zc - 1) / zc);
-    const bool hs = L.hs[0] != nullptr;
     const bool prec = L.precession != 0;
-    const bool store = L.st_n[0][0] != nullptr;
     cudaError_t e;
     if (store) {
         for (int c = 0; c < 3; ++c) {
@@ -270,7 +317,9 @@ cudaError_t launch_step_patch(const StepLaunch<float>& L) {
         a.dt = (float)L.dt;
     }
     TmaMaps maps;
-    if (!store && tma_applies(a, S) && encode_tma_maps(a, &maps)) {
+    if (tmem) {
+        e = prec ? patch_tmem_launch<true>(a, grid, L.stream, false) : patch_tmem_launch<false>(a, grid, L.stream, false);
+    } else if (use_tma && encode_tma_maps(a, &maps)) {
         e = patch_tma_dispatch<4>(a, &maps, grid, L.stream, prec, hs, store, false);
     } else if (store) {
         e = S == 4 ? patch_store_dispatch<4>(a, grid, L.stream, prec, hs, false)

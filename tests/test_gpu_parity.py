@@ -215,6 +215,29 @@ def test_tma_staging_bitwise(gpu, shape, hsite, bc, monkeypatch):
     assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("shape,precession,bc", [((128, 128, 40), 1, 0), ((64, 57, 33), 0, 1), ((37, 21, 13), 1, 0),
+                                                  ((2, 3, 5), 1, 1), ((1, 1, 1), 0, 0), ((96, 100, 70), 1, 1)])
+def test_tmem_rings_bitwise(gpu, shape, precession, bc, monkeypatch):
+    """The RK4 step with its older spin planes and accumulators in tensor
+    memory (28-row tiles; SPIN_TMEM=1 forces it) gives bitwise the states of
+    the register-ring step (SPIN_TMEM=0) over 20 steps with two pulses, on
+    ragged, tiny and free-boundary lattices and both equations: the same
+    arithmetic per site, only where the values wait between iterations
+    differs."""
+    nx, ny, nz = shape
+    p = gpu.Params(nx, ny, nz, J=1.0, D=0.05, H=(0.01, -0.02, 0.02), lam=0.05, T=1.0, dt=0.1, R=10, seed=3,
+                   precision=32, bc=bc, precession=precession)
+    s0 = spin_inputs.random_spins(nx, ny, nz, seed=2)
+    monkeypatch.setenv("SPIN_TMEM", "1")
+    a, la = run_gpu(gpu, p, s0, 20)
+    monkeypatch.setenv("SPIN_TMEM", "0")
+    b, lb = run_gpu(gpu, p, s0, 20)
+    monkeypatch.delenv("SPIN_TMEM", raising=False)
+    la.close()
+    lb.close()
+    assert np.array_equal(a, b)
+
+
 # ----------------------------------------------------------------- graph path, resume
 @pytest.mark.parametrize("R", [10, 5, 1])
 def test_graph_replay_equals_eager(gpu, R):
