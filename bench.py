@@ -636,6 +636,34 @@ def mc_timing(sp, torch, stream, hbm_peak):
     return out
 
 
+def time_pulse(torch, lat, R, intervals, stream, flush, plain_ms):
+    """Per-launch milliseconds of the noise-pulse kernel: CUDA events around
+    the two steps that straddle the pulse (step floor(R/2), which launches the
+    fused step and then the pulse kernel, and the plain step after it), minus
+    two plain steps.  Starts at the beginning of an interval."""
+    h = R // 2
+    if h < 1 or h + 1 >= R:
+        return None
+    pre = h - 1 if (h - 1) % 2 == 0 else h - 2      # an even run of plain steps before the pulse step
+    d = []
+    with torch.cuda.stream(stream):
+        for _ in range(intervals):
+            flush.zero_()
+            torch.cuda._sleep(3_000_000)
+            if pre:
+                lat.step(pre)
+            if h - 1 - pre:
+                lat.step(h - 1 - pre)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            lat.step(2)
+            b.record(stream)
+            d.append((a, b))
+            lat.step(R - h - 1)
+    torch.cuda.synchronize()
+    return float(np.mean([a.elapsed_time(b) for a, b in d])) - 2 * plain_ms
+
+
 def kernel_timing_256(sp, torch, dev, flush, stream, hbm_peak):
     """The same fused RK4 step on a 256^3 lattice (201 MB per state copy,
     larger than L2): plain-step launch time and its HBM fraction.  At this
@@ -761,6 +789,16 @@ def run_ours(args, ws, rank, local):
     achieved_tflops = RK4_FLOPS_PER_SPIN_STEP * N / t_kernel / 1e12
     alu_peak = SMS * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
     traffic = _ncu_traffic()
+    pulse_ms = time_pulse(torch, lat, R, max(3, args.steps), stream, flush, float(np.mean(kern_ms)))
+    pulse = None
+    if pulse_ms is not None and pulse_ms > 0:
+        pulse_gbs = BYTES_PER_SPIN_STEP_FP32 * N / (pulse_ms / 1e3) / 1e9
+        pulse = {"kernel": "k_pulse_f32 (Philox4x64-10 + Box-Muller + rotation, Eq. s_rotation)",
+                 "ms_per_launch": pulse_ms, "launches_per_step": 1.0 / R,
+                 "algorithmic_bytes_per_launch": BYTES_PER_SPIN_STEP_FP32 * N, "achieved_GBps": pulse_gbs,
+                 "frac_hbm": pulse_gbs / hbm_peak,
+                 "how": "the pulse step and the next plain step by CUDA events, minus two plain steps",
+                 "bound": "64-bit integer multiplies of the counter-based generator (20 per site)"}
 
     # end to end through the public API with host buffers
     host_in = torch.from_numpy(s0.astype(np.float32)).pin_memory()
@@ -841,6 +879,7 @@ def run_ours(args, ws, rank, local):
             "roofline": roof,
             "roofline_hbm": roof_hbm,
             "roofline_alu": roof_alu,
+            "pulse": pulse,
             "e2e": {"value": e2e_value, "unit": "spin-steps/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h,
                     "mode": "copies on their own streams, overlapped with the neighbouring intervals' compute",
