@@ -130,6 +130,13 @@ int spin_lattice_create(const spin_params* p, void* sx, void* sy, void* sz,
  * values at the end of each Delta t).  Full intervals are replayed from a
  * cached CUDA graph.  On return (stream-ordered) the caller's arrays hold the
  * state after the last step.
+ * Kernel choice for FP32 RK4 steps (all give bitwise the same states): the
+ * register-ring fused step, or, where its wave-cost estimate is lower (large
+ * lattices, no per-site field), the step that keeps its older planes in
+ * tensor memory; the environment variable SPIN_TMEM=0 / =1, read when a step
+ * is launched or captured, forbids / forces the latter, and SPIN_TMA=1
+ * stages the spin planes by tensor-map bulk copies instead of cp.async
+ * (slower on GB300; kept for measurement).
  * Errors: SPIN_EINVAL (null handle, nsteps < 0), SPIN_ECUDA.
  */
 int spin_step_pulse(spin_lattice* h, int64_t nsteps);
