@@ -16,10 +16,11 @@
 // lattices needs no z chunks at all.  The arithmetic of every site, and so
 // every result, is bitwise that of the register-ring kernel.
 //
-// Used for RK4 steps without per-site fields, stage stores or a fused pulse;
-// tcgen05.alloc takes 256 of the SM's 512 TMEM columns, and one CTA is
-// resident per SM (registers and shared memory), so the allocation never
-// waits.
+// Used for RK4 steps without per-site fields, stage stores or a fused pulse.
+// tcgen05.alloc takes 256 of the SM's 512 TMEM columns; the kernel's
+// registers and shared memory leave room for one of its CTAs per SM, so its
+// CTAs never compete for the columns (an allocation waits only while another
+// kernel's CTA on the same SM holds more than 256 of them).
 #pragma once
 #include "patch_tile.cuh"
 
