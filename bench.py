@@ -205,9 +205,9 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm), "sampled": where}
 
 
-# the sources k_step_patch is compiled from (its own file and the headers it includes)
-PATCH_KERNEL_SOURCES = ("step_patch.cu", "patch_tile.cuh", "patch_tmem.cuh", "patch_common.cuh", "spin_device.cuh",
-                        "spin_internal.h")
+# the sources k_step_patch's code comes from (the file that instantiates it and
+# the headers its device code is in)
+PATCH_KERNEL_SOURCES = ("step_patch.cu", "patch_tile.cuh", "patch_common.cuh", "spin_device.cuh", "spin_internal.h")
 
 
 def _kernel_source_hash():
