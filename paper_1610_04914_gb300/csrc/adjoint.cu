@@ -45,6 +45,44 @@ namespace {
 constexpr int kAT = 256;                 // threads per block (8 warps)
 constexpr int kAW = kAT / 32;
 
+// Programmatic dependent launch of the transposed-step kernels: each is
+// launched while the kernel before it drains, and waits (griddepcontrol.wait,
+// a no-op without a programmatic dependency) for that kernel's completion and
+// memory before touching global memory; each lets its successor launch once
+// all of its blocks have stored their results.
+#ifndef SPIN_ADJ_PDL
+#define SPIN_ADJ_PDL 1
+#endif
+__device__ __forceinline__ void pdl_wait() {
+#if SPIN_ADJ_PDL
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+#endif
+}
+__device__ __forceinline__ void pdl_trigger() {
+#if SPIN_ADJ_PDL
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+#endif
+}
+template <typename Kern, typename... Args>
+cudaError_t pdl_launch(Kern kernel, dim3 grid, cudaStream_t st, Args... args) {
+#if SPIN_ADJ_PDL
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(kAT);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+#else
+    kernel<<<grid, kAT, 0, st>>>(args...);
+    return cudaGetLastError();
+#endif
+}
+
 // A site of the lattice with its six neighbours (x-1, x+1, y-1, y+1, z-1, z+1;
 // periodic wrap) and their weights (0 across a face of a free-boundary
 // lattice).  All indices fit in 32 bits (N < 2^31).
@@ -326,9 +364,11 @@ __device__ __forceinline__ void top_body(const TopArgs<real>& a, const AdjGeom<r
 
 template <typename real, bool PREC, bool HSITE, int S, bool CHAIN>
 __global__ void __launch_bounds__(kAT) k_adj_top_w(TopArgs<real> a, AdjGeom<real> G) {
+    pdl_wait();
     const Site<real> st = site_here<real>(G.nx, G.ny, G.nz, G.bc);
     const int i = st.i;
     top_body<real, PREC, HSITE, S, CHAIN>(a, G, st, a.lam.c[0][i], a.lam.c[1][i], a.lam.c[2][i]);
+    pdl_trigger();
 }
 
 // Stage j of the transposed step: the neighbour part ("x-part") of stage j,
@@ -355,6 +395,7 @@ struct XWArgs {
 
 template <typename real, bool PREC, bool HSITE, int NL, bool W, bool CHAIN>
 __global__ void __launch_bounds__(kAT) k_adj_xw(XWArgs<real> a, AdjGeom<real> G) {
+    pdl_wait();
     const Site<real> st = site_here<real>(G.nx, G.ny, G.nz, G.bc);
     const int i = st.i;
     constexpr int NLOAD = CHAIN ? 1 : (NL > 0 ? NL : 1);
@@ -400,6 +441,7 @@ __global__ void __launch_bounds__(kAT) k_adj_xw(XWArgs<real> a, AdjGeom<real> G)
         const real v[3] = {G.dt * lk[0], G.dt * lk[1], G.dt * lk[2]};
         w_part<real, PREC, HSITE>(a.prev, a.hs, st, G, v, a.wn, a.un, a.gh, a.gjd);
     }
+    pdl_trigger();
 }
 
 // The first stage's x-part of step m (lam_s += lx, final: the adjoint of step
@@ -409,6 +451,7 @@ __global__ void __launch_bounds__(kAT) k_adj_xw(XWArgs<real> a, AdjGeom<real> G)
 // arrays of step m-1).
 template <typename real, bool PREC, bool HSITE, int S, bool CHAIN>
 __global__ void __launch_bounds__(kAT) k_adj_x0_top(XWArgs<real> a, TopArgs<real> ta, AdjGeom<real> G) {
+    pdl_wait();
     const Site<real> st = site_here<real>(G.nx, G.ny, G.nz, G.bc);
     const int i = st.i;
     real ux[3], lm[3], nsum[3];
@@ -427,6 +470,7 @@ __global__ void __launch_bounds__(kAT) k_adj_x0_top(XWArgs<real> a, TopArgs<real
         l[c] = lm[c] + lx;
     }
     top_body<real, PREC, HSITE, S, CHAIN>(ta, G, st, l[0], l[1], l[2]);
+    pdl_trigger();
 }
 
 // FP64 sums of kSumParts consecutive parts of each of the arrays at v + c N
@@ -580,21 +624,21 @@ cudaError_t launch_xw_t(int j, int S, bool chain, const XWArgs<real>& a, const A
     if (!adj_tableau_supported(S, chain)) return cudaErrorInvalidValue;
     if (chain) {
         switch (j) {
-            case 0: k_adj_xw<real, PREC, HSITE, 0, false, true><<<gb, kAT, 0, st>>>(a, G); break;
-            case 1: k_adj_xw<real, PREC, HSITE, 1, true, true><<<gb, kAT, 0, st>>>(a, G); break;
-            case 2: k_adj_xw<real, PREC, HSITE, 2, true, true><<<gb, kAT, 0, st>>>(a, G); break;
-            case 3: k_adj_xw<real, PREC, HSITE, 3, true, true><<<gb, kAT, 0, st>>>(a, G); break;
+            case 0: return pdl_launch(k_adj_xw<real, PREC, HSITE, 0, false, true>, gb, st, a, G);
+            case 1: return pdl_launch(k_adj_xw<real, PREC, HSITE, 1, true, true>, gb, st, a, G);
+            case 2: return pdl_launch(k_adj_xw<real, PREC, HSITE, 2, true, true>, gb, st, a, G);
+            case 3: return pdl_launch(k_adj_xw<real, PREC, HSITE, 3, true, true>, gb, st, a, G);
             default: return cudaErrorInvalidValue;
         }
         return cudaSuccess;
     }
     switch (j) {
-        case 0: k_adj_xw<real, PREC, HSITE, 0, false, false><<<gb, kAT, 0, st>>>(a, G); break;
-        case 1: k_adj_xw<real, PREC, HSITE, 1, true, false><<<gb, kAT, 0, st>>>(a, G); break;
-        case 2: k_adj_xw<real, PREC, HSITE, 2, true, false><<<gb, kAT, 0, st>>>(a, G); break;
-        case 3: k_adj_xw<real, PREC, HSITE, 3, true, false><<<gb, kAT, 0, st>>>(a, G); break;
-        case 4: k_adj_xw<real, PREC, HSITE, 4, true, false><<<gb, kAT, 0, st>>>(a, G); break;
-        case 5: k_adj_xw<real, PREC, HSITE, 5, true, false><<<gb, kAT, 0, st>>>(a, G); break;
+        case 0: return pdl_launch(k_adj_xw<real, PREC, HSITE, 0, false, false>, gb, st, a, G);
+        case 1: return pdl_launch(k_adj_xw<real, PREC, HSITE, 1, true, false>, gb, st, a, G);
+        case 2: return pdl_launch(k_adj_xw<real, PREC, HSITE, 2, true, false>, gb, st, a, G);
+        case 3: return pdl_launch(k_adj_xw<real, PREC, HSITE, 3, true, false>, gb, st, a, G);
+        case 4: return pdl_launch(k_adj_xw<real, PREC, HSITE, 4, true, false>, gb, st, a, G);
+        case 5: return pdl_launch(k_adj_xw<real, PREC, HSITE, 5, true, false>, gb, st, a, G);
         default: return cudaErrorInvalidValue;
     }
     return cudaSuccess;
@@ -615,8 +659,8 @@ cudaError_t launch_xw(bool prec, bool hsite, int j, int S, bool chain, const XWA
 template <typename real, bool PREC, bool HSITE>
 cudaError_t launch_x0_top_t(int S, bool chain, const XWArgs<real>& xa, const TopArgs<real>& ta, const AdjGeom<real>& G,
                             dim3 gb, cudaStream_t st) {
-    if (chain && S == 2) k_adj_x0_top<real, PREC, HSITE, 2, true><<<gb, kAT, 0, st>>>(xa, ta, G);
-    else if (chain && S == 4) k_adj_x0_top<real, PREC, HSITE, 4, true><<<gb, kAT, 0, st>>>(xa, ta, G);
+    if (chain && S == 2) return pdl_launch(k_adj_x0_top<real, PREC, HSITE, 2, true>, gb, st, xa, ta, G);
+    else if (chain && S == 4) return pdl_launch(k_adj_x0_top<real, PREC, HSITE, 4, true>, gb, st, xa, ta, G);
     else return cudaErrorInvalidValue;
     return cudaSuccess;
 }
@@ -635,9 +679,9 @@ cudaError_t launch_x0_top(bool prec, bool hsite, int S, bool chain, const XWArgs
 template <typename real, bool PREC, bool HSITE>
 cudaError_t launch_top_w_t(int S, bool chain, const TopArgs<real>& a, const AdjGeom<real>& G, dim3 gb,
                            cudaStream_t st) {
-    if (chain && S == 2) k_adj_top_w<real, PREC, HSITE, 2, true><<<gb, kAT, 0, st>>>(a, G);
-    else if (chain && S == 4) k_adj_top_w<real, PREC, HSITE, 4, true><<<gb, kAT, 0, st>>>(a, G);
-    else if (!chain && S == 6) k_adj_top_w<real, PREC, HSITE, 6, false><<<gb, kAT, 0, st>>>(a, G);
+    if (chain && S == 2) return pdl_launch(k_adj_top_w<real, PREC, HSITE, 2, true>, gb, st, a, G);
+    else if (chain && S == 4) return pdl_launch(k_adj_top_w<real, PREC, HSITE, 4, true>, gb, st, a, G);
+    else if (!chain && S == 6) return pdl_launch(k_adj_top_w<real, PREC, HSITE, 6, false>, gb, st, a, G);
     else return cudaErrorInvalidValue;
     return cudaSuccess;
 }
